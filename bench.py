@@ -1,0 +1,343 @@
+#!/usr/bin/env python
+"""Throughput of the compressed-sensing PAT operators: A + A^T pairs per second.
+
+Workload (default `c2`): 64x128x128 grid (z, y, x), dx = 100 um, c = 1500 m/s, CFL 0.3 (dt = 20 ns),
+T = 400 recorded steps, 10-voxel PML, random single-point sampling of 2048 of the 16384 detection
+plane points, a 20-tube synthetic vessel phantom.  One step = one forward A (p0 -> f = C A p0)
+plus one adjoint (f -> A^T C^T f) on each of `--batch` independent volumes, inputs resident on the
+GPU.  Between steps a 256 MiB buffer is written (inside the timed region) so that no step starts
+with the previous step's data in the 129 MB L2.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B] [--workload c2]
+    python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores, same metric
+
+Multi-GPU: replicas only (torchrun, one rank per GPU, independent volumes, no collective on the
+data path); value = pairs processed by all ranks / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "A+A^T pairs/s (64x128x128, 400 steps)"
+UNIT = "pairs/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--batch", type=int, default=1)
+    ap.add_argument("--workload", default="c2")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload_config(w, batch):
+    g, s = w.grid, w.sampling
+    kinds = {0: "full plane", 1: "rSP", 2: "sHd 0/1", 3: "sHd +-1"}
+    return {
+        "workload": (f"{w.name}: {g.nz}x{g.ny}x{g.nx} (z,y,x), dx {g.dx * 1e6:g} um, c {g.c:g} m/s, "
+                     f"CFL {g.cfl:g} (dt {g.dt * 1e9:g} ns), T {g.T}, {g.pml_size}-pt PML, "
+                     f"{kinds[s.kind]} {s.m}/{g.m_plane}, {w.phantom} phantom"),
+        "batch": batch,
+        "step": "one forward A and one adjoint A^T per volume",
+        "l2_flush": "256 MiB buffer written between steps, inside the timed region",
+    }
+
+
+# ------------------------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    """nvidia-smi samples (every 200 ms) while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.t = threading.Thread(target=self._read, daemon=True)
+        self.t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 8:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if r[4 + i].lower() == "active"})
+        sm_sorted = sorted(sm)
+        med = sm_sorted[len(sm_sorted) // 2] if sm_sorted else None
+        return {"sm_mhz": med, "sm_max_mhz": max(mx) if mx else None, "reasons": reasons,
+                "samples": len(self.rows)}
+
+
+# ------------------------------------------------------------------------------------ CPU oracle
+
+def oracle_pairs_per_s(w, n_steps_sample):
+    """Time the FP64 oracle's A + A^T on the full grid with n_steps_sample recorded steps and scale to
+    the full T by the step count.  Returns (pairs/s, seconds, threads)."""
+    import numpy as np
+
+    import oracle
+    from paper_1605_00133_gb300 import presets
+    ws = presets.shrink(w, n_steps_sample)
+    g, s = ws.grid, ws.sampling
+    p0 = w.p0()
+    y = np.random.default_rng(0).standard_normal((g.T, s.m))
+    t0 = time.perf_counter()
+    oracle.forward(g, s, p0)
+    oracle.adjoint(g, s, y)
+    t = time.perf_counter() - t0
+    scale = (w.grid.T - 1) / (n_steps_sample - 1)
+    return 1.0 / (t * scale), t, oracle.num_threads()
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    from paper_1605_00133_gb300 import presets
+    oracle.build()
+    w = presets.workload(args.workload)
+    Ts = 4
+    for _ in range(args.warmup):
+        oracle_pairs_per_s(w, Ts)
+    tot = 0.0
+    for _ in range(args.steps):
+        _, t, threads = oracle_pairs_per_s(w, Ts)
+        tot += t
+    scale = (w.grid.T - 1) / (Ts - 1)
+    sec_per_pair = tot / args.steps * scale
+    value = 1.0 / sec_per_pair
+    sample = (f"each step: oracle A + A^T on the full {w.grid.nz}x{w.grid.ny}x{w.grid.nx} grid with "
+              f"T = {Ts} ({Ts - 1} time steps each way), scaled by {scale:.1f} to T = {w.grid.T}")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec_per_pair * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(w, 1),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------------------------ GPU arm
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if dist:
+        dist.barrier()
+    __graft_entry__.build()
+
+    from paper_1605_00133_gb300 import presets
+    from paper_1605_00133_gb300.operators import PatOperator
+
+    w = presets.workload(args.workload)
+    B = args.batch
+    g = w.grid
+    gb = presets.Grid(g.nz, g.ny, g.nx, dx=g.dx, c=g.c, rho0=g.rho0, cfl=g.cfl, T=g.T,
+                      pml_size=g.pml_size, pml_alpha=g.pml_alpha, sensor_z=g.sensor_z, batch=B)
+    op = PatOperator(gb, w.sampling)
+    p0_np = np.stack([w.p0(seed_offset=100 * rank + b) for b in range(B)]).astype(np.float32)
+    p0 = torch.tensor(p0_np, device=dev)
+    f = torch.empty(op.data_shape, device=dev)
+    p = torch.empty(op.image_shape, device=dev)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
+
+    def step():
+        op.forward_into(p0, f)
+        op.adjoint_into(f, p)
+        flush.fill_(1.0)
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x):
+        if not dist:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    barrier()
+    ms = max_over_ranks(ms)
+    pairs = B * world * args.steps
+    value = pairs / (ms / 1e3)
+
+    # per-kernel breakdown: the same K steps again with every launch bracketed by CUDA events on the
+    # launching stream (torch's current stream, which the library uses)
+    op.profile(True)
+    for _ in range(args.steps):
+        step()
+    prof = op.profile_read()
+    op.profile(False)
+    total_prof = sum(v[0] for v in prof.values())
+    launches_per_step = sum(v[1] for v in prof.values()) / args.steps
+    kernels = {k: {"ms_total": v[0], "launches": v[1], "avg_us": 1e3 * v[0] / v[1],
+                   "share": v[0] / total_prof} for k, v in prof.items()}
+    dominant = max(kernels, key=lambda k: kernels[k]["ms_total"])
+
+    # roofline: the time step is the unit of work (SURVEY 48 bytes per voxel per step: six FP32
+    # state fields read and written once); one step = 4 launches on one stream
+    import json as _json
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peak, peak_src = 6800.0, "fallback 6.8 TB/s"
+    if os.path.exists(peaks_path):
+        pk = _json.load(open(peaks_path))
+        peak, peak_src = float(pk["hbm_gbs"]), "measured hbm_gbs"
+    steps_per_pair = 2 * (g.T - 1)
+    step_s = (ms / 1e3) / (args.steps * steps_per_pair)
+    bytes_per_step = 48.0 * g.n * B
+    achieved = bytes_per_step / step_s / 1e9
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic_per_step.json")
+    if os.path.exists(tpath):
+        try:
+            tt = _json.load(open(tpath))
+            if tt.get("workload") == w.name and tt.get("batch") == B and tt.get("source_hash") == _source_hash():
+                traffic = tt["dram_bytes_per_step"]
+        except Exception:
+            traffic = None
+    roofline = {"bound": "hbm", "kernel": "time step (zpass_grad3 + plane_vel + zpass_each3 + plane_rho_fwd, "
+                                          "and the adjoint's four)",
+                "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": traffic, "peak_source": peak_src,
+                "algorithmic_bytes_per_unit": "48 B per voxel per time step",
+                "dominant_kernel": dominant, "dominant_share": kernels[dominant]["share"],
+                "dominant_avg_us": kernels[dominant]["avg_us"]}
+
+    # end to end through the public API: pinned host p0 -> device, A, A^T, device -> pinned host
+    e2e = None
+    if not args.no_e2e:
+        p0_h = torch.tensor(p0_np).pin_memory()
+        p_h = torch.empty(op.image_shape, dtype=torch.float32).pin_memory()
+        p0_d = torch.empty_like(p0)
+
+        def step_e2e():
+            p0_d.copy_(p0_h, non_blocking=True)
+            op.forward_into(p0_d, f)
+            op.adjoint_into(f, p)
+            p_h.copy_(p, non_blocking=True)
+            flush.fill_(1.0)
+
+        for _ in range(max(1, args.warmup)):
+            step_e2e()
+        barrier()
+        e0.record()
+        for _ in range(args.steps):
+            step_e2e()
+        e1.record()
+        torch.cuda.synchronize()
+        ms_e2e = max_over_ranks(e0.elapsed_time(e1))
+        e2e = {"value": pairs / (ms_e2e / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": int(p0_h.numel() * 4), "d2h_bytes_per_step": int(p_h.numel() * 4)}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        Ts = 16
+        v, t, threads = oracle_pairs_per_s(w, Ts)
+        cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": (f"one oracle A + A^T on the full {g.nz}x{g.ny}x{g.nx} grid with T = {Ts} "
+                          f"({Ts - 1} time steps each way, {t:.1f} s), scaled to T = {g.T}")}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": workload_config(w, B), "clocks": clk, "e2e": e2e,
+                "gpu_launches": int(round(launches_per_step * args.steps)),
+                "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu}
+        print(json.dumps(line), flush=True)
+    op.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def _source_hash():
+    import hashlib
+    h = hashlib.sha1()
+    d = os.path.join(ROOT, "paper_1605_00133_gb300", "csrc")
+    for n in sorted(os.listdir(d)):
+        if n.endswith((".cu", ".cuh", ".h")):
+            h.update(open(os.path.join(d, n), "rb").read())
+    return h.hexdigest()[:12]
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,145 @@
+/*
+ * pat.h - C ABI of libpat: the photoacoustic forward operator A, its exact adjoint A^T and the
+ * sub-sampling operator C of compressed-sensing PAT (Arridge et al., "Accelerated High-Resolution
+ * Photoacoustic Tomography via Compressed Sensing", arXiv:1605.00133), as CUDA kernels for one
+ * GB300 GPU (sm_103a).
+ *
+ * Model (Sec. 2.1, Eq. PATfwd; discrete model Sec. 4.3):
+ *   (d_tt - c^2 Laplace) p = 0,  p(t=0) = p0,  d_t p(t=0) = 0,
+ * solved by explicit k-space pseudospectral time stepping on an Nz x Ny x Nx grid of voxel size dx
+ * with the time step equal to the sampling interval.  The detection plane is the grid plane
+ * z = sensor_z (z is the depth axis, the paper's x).  A maps p0 to the plane pressure at the T
+ * recorded steps n = 0..T-1 (n = 0 is p0 itself); C samples each recorded plane (Sec. 3.1,
+ * Eq. GenScan): all points, a list of single points (rSP / gSP), or binary scrambled-Hadamard
+ * patterns (sHd, Sec. 4.3).  Data are f = C A p0 (Eq. Fwd); back-projection is A^T C^T f (Eq. BP).
+ *
+ * Discretisation fixed by this library (the paper defers it to k-Wave):
+ *   kappa(k) = sinc(c dt |k| / 2);  D_i^{+/-} f = Re F^-1[ i k_i kappa exp(+/- i k_i dx/2) F f ]
+ *   rho_i^0 = p0/(3c^2),  u_i^{-1/2} = dt/(2 rho0) D_i^+ p0
+ *   u_i^{n+1/2} = as_i (as_i u_i^{n-1/2} - dt/rho0 D_i^+ p^n)
+ *   rho_i^{n+1} = a_i (a_i rho_i^n - dt rho0 D_i^- u_i^{n+1/2}),   p^{n+1} = c^2 sum_i rho_i^{n+1}
+ *   a_i = exp(-alpha_i dt/2), alpha_i = pml_alpha (c/dx) (d/P)^4 at depth d voxels into the
+ *   P = pml_size layer on each face (zero inside); as_i on the staggered points j + 1/2.
+ *
+ * Conventions
+ *   Memory: all array arguments named *_dev are device pointers owned by the caller, FP32 (or int32
+ *   where stated), contiguous and at least 16-byte aligned.  The library owns its workspace, which
+ *   pat_create_grid allocates and pat_destroy_grid frees.
+ *   Streams: every call is ordered on the given cudaStream_t (pass NULL for the legacy default
+ *   stream) and returns without synchronising the device.
+ *   Threads: a grid handle must not be used by two streams or threads at the same time.
+ *   Errors: arguments are checked before anything is launched; on failure nothing is launched, the
+ *   call returns a non-zero pat_status and pat_last_error() describes it.  No C++ exception crosses
+ *   this interface.  There is no CPU fallback: without a usable GPU, calls fail with PAT_ERR_CUDA.
+ */
+#ifndef PAT_H
+#define PAT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PAT_OK = 0,
+    PAT_ERR_INVALID_ARG = 1,   /* bad pointer, size, descriptor or index set */
+    PAT_ERR_CUDA = 2,          /* a CUDA runtime call or kernel launch failed */
+    PAT_ERR_OOM = 3,           /* device workspace could not be allocated */
+    PAT_ERR_TIMEOUT = 4,       /* reserved: a bounded device-side wait gave up */
+    PAT_ERR_NOT_CONVERGED = 5, /* reserved for iterative solvers */
+    PAT_ERR_UNSUPPORTED = 6    /* valid request this build does not handle (e.g. grid too large) */
+} pat_status;
+
+/* Sampling operator C (Sec. 3.1, Sec. 4.3). */
+typedef enum {
+    PAT_SAMPLE_FULL = 0,        /* conventional scan: every plane point, m = Ny*Nx */
+    PAT_SAMPLE_POINTS = 1,      /* rSP/gSP: m distinct plane points (row selection) */
+    PAT_SAMPLE_HADAMARD01 = 2,  /* sHd, binary 0/1 patterns phi_j(perm[l]) = (1 + H[rows_j][l]) / 2 */
+    PAT_SAMPLE_HADAMARDPM = 3   /* sHd, +-1/sqrt(M) patterns phi_j(perm[l]) = H[rows_j][l] / sqrt(M) */
+} pat_sampling_kind;
+
+typedef struct pat_grid pat_grid; /* opaque; owns the device workspace and constant tables */
+
+typedef struct {
+    int32_t nz, ny, nx;   /* grid size, (z, y, x) with x fastest; each a power of two in [8, 256] */
+    double dx;            /* voxel size in metres (isotropic), > 0 */
+    double c;             /* sound speed in m/s, > 0 */
+    double rho0;          /* ambient density, > 0 (does not affect p) */
+    double cfl;           /* used when dt <= 0: dt = cfl * dx / c */
+    double dt;            /* time step in seconds (= sampling interval); <= 0 selects cfl */
+    int32_t T;            /* number of recorded samples n = 0..T-1, >= 1 */
+    int32_t pml_size;     /* absorbing layer thickness in voxels on every face, 0 <= 2*P < min(n) */
+    double pml_alpha;     /* absorption at full layer depth, nepers per voxel (e.g. 2.0) */
+    int32_t sensor_z;     /* detection plane index in [0, nz); < 0 selects pml_size */
+    int32_t batch;        /* number of independent volumes B processed per call, >= 1 */
+} pat_grid_desc;
+
+typedef struct {
+    int32_t kind;             /* pat_sampling_kind */
+    int32_t m;                /* M_c, number of measurements per time step (FULL: ignored) */
+    const int32_t* indices;   /* host, POINTS: int32[m] distinct plane indices y*Nx + x */
+    const int32_t* perm;      /* host, HADAMARD*: int32[Ny*Nx], a permutation (pattern scramble) */
+    const int32_t* rows;      /* host, HADAMARD*: int32[m] distinct Hadamard rows in [0, Ny*Nx) */
+} pat_sampling_desc;
+
+/* Create a grid: validates both descriptors, copies the index sets, builds the k-space, PML and
+ * FFT tables (in double precision, stored as FP32) and allocates the device workspace on the
+ * current CUDA device.  The handle stays bound to that device.  Returns PAT_OK and *out, or an
+ * error with *out = NULL.  HADAMARD kinds need Ny*Nx a power of two and at most 32768. */
+pat_status pat_create_grid(const pat_grid_desc* desc, const pat_sampling_desc* sampling,
+                           pat_grid** out);
+
+/* Free the grid and its device workspace (waits for work queued on the device to finish).
+ * NULL is accepted. */
+void pat_destroy_grid(pat_grid* grid);
+
+/* Sizes of one batch entry: n_image = Nz*Ny*Nx, n_data = T*m; plus m and the time step dt. Any
+ * output pointer may be NULL. */
+pat_status pat_grid_info(const pat_grid* grid, int64_t* n_image, int64_t* n_data, int32_t* m,
+                         double* dt);
+
+/* Bytes of device workspace the grid holds. */
+int64_t pat_workspace_bytes(const pat_grid* grid);
+
+/* f = C A p0 (Sec. 4.3, Eq. Fwd without noise).
+ *   p0_dev: float[B][Nz][Ny][Nx] (read only);  f_dev: float[B][T][m] (overwritten).
+ * p0_dev and f_dev must not overlap. */
+pat_status pat_forward(pat_grid* grid, const float* p0_dev, float* f_dev, void* cuda_stream);
+
+/* p = A^T C^T f (Sec. 4.4, Eq. BP: the exact transpose of pat_forward).
+ *   f_dev: float[B][T][m] (read only);  p_dev: float[B][Nz][Ny][Nx] (overwritten).
+ * f_dev and p_dev must not overlap. */
+pat_status pat_adjoint(pat_grid* grid, const float* f_dev, float* p_dev, void* cuda_stream);
+
+/* C alone, applied to a plane series (Sec. 3.1, Eq. GenScan per time point):
+ *   pbar_dev: float[B][nt][Ny*Nx] -> f_dev: float[B][nt][m].  nt >= 1. */
+pat_status pat_sample(pat_grid* grid, const float* pbar_dev, float* f_dev, int32_t nt,
+                      void* cuda_stream);
+
+/* C^T alone: f_dev float[B][nt][m] -> pbar_dev float[B][nt][Ny*Nx] (overwritten; rSP zero-fills). */
+pat_status pat_sample_adjoint(pat_grid* grid, const float* f_dev, float* pbar_dev, int32_t nt,
+                              void* cuda_stream);
+
+/* Kernel timing for benchmarks: while enabled, every kernel launch of pat_forward / pat_adjoint is
+ * bracketed by CUDA events recorded on the call's stream.  pat_profile_enable(grid, 1) starts (and
+ * clears) the record; pat_profile_read waits for the recorded events, then reports per kernel class
+ * its name (NUL-terminated, at most 47 characters, in names[48*i]), total device milliseconds and
+ * launch count.  Classes: plane_init, plane_vel, plane_rho_fwd, plane_rho_adj, zpass_grad3,
+ * zpass_each3, zpass_sum3, sample (see pat_kernels.cu).  n_classes receives the number written
+ * (<= max_classes). */
+pat_status pat_profile_enable(pat_grid* grid, int32_t enable);
+pat_status pat_profile_read(pat_grid* grid, int32_t max_classes, char* names, double* total_ms,
+                            int64_t* launches, int32_t* n_classes);
+
+/* Message for the last failed call on this thread ("" if none). Valid until the next call. */
+const char* pat_last_error(void);
+
+/* Library version string. */
+const char* pat_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PAT_H */

@@ -1,0 +1,430 @@
+// pat_api.cu - C ABI of libpat: argument checking, constant tables, workspace, dispatch.
+//
+// Constant tables are computed here in double precision and stored as FP32:
+//   FFT twiddles exp(-2 pi i m / L) per axis;
+//   kappa(|k|) / N on the half spectrum, kappa = sinc(c dt |k| / 2) (the k-space correction that
+//   makes the leapfrog step exact per plane wave; the 1/N of the inverse 3D FFT is folded in);
+//   i k exp(+/- i k dx / 2) per axis (staggered spectral derivative factors; the Nyquist bin
+//   k = -pi/dx gives a real factor, so every operator maps real fields to real fields);
+//   split-field PML factors a = exp(-alpha dt / 2), alpha = pml_alpha (c/dx) (d/P)^4, on regular
+//   (j) and staggered (j + 1/2) points, and the per-axis update coefficients built from them.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <complex>
+#include <string>
+#include <vector>
+
+#include "pat_internal.h"
+
+using namespace pat;
+
+namespace {
+
+thread_local std::string g_err;
+
+pat_status fail(pat_status s, const std::string& msg) {
+    g_err = msg;
+    return s;
+}
+
+pat_status cuda_fail(cudaError_t e, const char* where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return fail(e == cudaErrorMemoryAllocation ? PAT_ERR_OOM : PAT_ERR_CUDA, m);
+}
+
+bool pow2_in(int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; }
+
+}  // namespace
+
+struct pat_grid {
+    pat_grid_desc d;
+    int kind;
+    int m;
+    int device;
+    Geom g;
+    Scalars s;
+    DeviceTables t;
+    Workspace w;
+    std::vector<void*> allocs;
+    int64_t bytes;
+    Profiler prof;
+};
+
+namespace {
+
+pat_status dalloc(pat_grid* G, void** p, size_t bytes, const char* what) {
+    *p = nullptr;
+    if (bytes == 0) return PAT_OK;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? PAT_ERR_OOM : PAT_ERR_CUDA,
+                    std::string("cudaMalloc(") + what + ", " + std::to_string(bytes) + " bytes): " + cudaGetErrorString(e));
+    }
+    G->allocs.push_back(*p);
+    G->bytes += (int64_t)bytes;
+    return PAT_OK;
+}
+
+template <class T>
+pat_status upload(pat_grid* G, T** dst, const std::vector<T>& host, const char* what) {
+    pat_status s = dalloc(G, (void**)dst, host.size() * sizeof(T), what);
+    if (s != PAT_OK) return s;
+    if (host.empty()) return PAT_OK;
+    cudaError_t e = cudaMemcpy(*dst, host.data(), host.size() * sizeof(T), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(table)");
+    return PAT_OK;
+}
+
+void free_grid(pat_grid* G) {
+    if (!G) return;
+    for (void* p : G->allocs) cudaFree(p);
+    for (cudaEvent_t e : G->prof.pool) cudaEventDestroy(e);
+    delete G;
+}
+
+double wavenumber(int m, int n, double dx) {
+    const int mm = (m < n / 2) ? m : m - n;  // Nyquist bin negative
+    return 2.0 * M_PI * (double)mm / ((double)n * dx);
+}
+
+// PML factor exp(-alpha dt/2) at a (possibly staggered) position along an axis of n points
+double pml_factor(const pat_grid_desc& d, double dt, double pos, int n) {
+    const int P = d.pml_size;
+    if (P <= 0) return 1.0;
+    double depth = 0.0;
+    if (pos < (double)P) depth = (double)P - pos;
+    else if (pos > (double)(n - 1 - P)) depth = pos - (double)(n - 1 - P);
+    if (depth <= 0.0) return 1.0;
+    const double r = depth / (double)P;
+    const double alpha = d.pml_alpha * (d.c / d.dx) * r * r * r * r;
+    return exp(-alpha * dt / 2.0);
+}
+
+pat_status validate(const pat_grid_desc* d, const pat_sampling_desc* sm) {
+    if (!d || !sm) return fail(PAT_ERR_INVALID_ARG, "pat_create_grid: NULL descriptor");
+    if (!pow2_in(d->nz, 8, 256) || !pow2_in(d->ny, 8, 256) || !pow2_in(d->nx, 8, 256))
+        return fail(PAT_ERR_INVALID_ARG, "grid sizes must be powers of two in [8, 256]");
+    if (!(d->dx > 0) || !(d->c > 0) || !(d->rho0 > 0))
+        return fail(PAT_ERR_INVALID_ARG, "dx, c and rho0 must be positive");
+    if (!(d->dt > 0) && !(d->cfl > 0)) return fail(PAT_ERR_INVALID_ARG, "need dt > 0 or cfl > 0");
+    if (d->T < 1) return fail(PAT_ERR_INVALID_ARG, "T must be >= 1");
+    if (d->batch < 1) return fail(PAT_ERR_INVALID_ARG, "batch must be >= 1");
+    const int mn = std::min(d->nz, std::min(d->ny, d->nx));
+    if (d->pml_size < 0 || 2 * d->pml_size >= mn)
+        return fail(PAT_ERR_INVALID_ARG, "pml_size must satisfy 0 <= 2*pml_size < min(nz, ny, nx)");
+    if (!(d->pml_alpha >= 0)) return fail(PAT_ERR_INVALID_ARG, "pml_alpha must be >= 0");
+    const int sz = d->sensor_z < 0 ? d->pml_size : d->sensor_z;
+    if (sz >= d->nz) return fail(PAT_ERR_INVALID_ARG, "sensor_z out of range");
+    const int M = d->ny * d->nx;
+    switch (sm->kind) {
+        case PAT_SAMPLE_FULL: break;
+        case PAT_SAMPLE_POINTS: {
+            if (sm->m < 0 || sm->m > M) return fail(PAT_ERR_INVALID_ARG, "POINTS: need 0 <= m <= Ny*Nx");
+            if (sm->m > 0 && !sm->indices) return fail(PAT_ERR_INVALID_ARG, "POINTS: indices is NULL");
+            std::vector<char> seen(M, 0);
+            for (int j = 0; j < sm->m; j++) {
+                const int v = sm->indices[j];
+                if (v < 0 || v >= M) return fail(PAT_ERR_INVALID_ARG, "POINTS: index out of range");
+                if (seen[v]) return fail(PAT_ERR_INVALID_ARG, "POINTS: duplicate index");
+                seen[v] = 1;
+            }
+            break;
+        }
+        case PAT_SAMPLE_HADAMARD01:
+        case PAT_SAMPLE_HADAMARDPM: {
+            if ((M & (M - 1)) != 0) return fail(PAT_ERR_INVALID_ARG, "HADAMARD: Ny*Nx must be a power of two");
+            if (M > 32768) return fail(PAT_ERR_UNSUPPORTED, "HADAMARD: Ny*Nx above 32768 is not supported");
+            if (sm->m < 1 || sm->m > M) return fail(PAT_ERR_INVALID_ARG, "HADAMARD: need 1 <= m <= Ny*Nx");
+            if (!sm->perm || !sm->rows) return fail(PAT_ERR_INVALID_ARG, "HADAMARD: perm/rows is NULL");
+            std::vector<char> seen(M, 0);
+            for (int l = 0; l < M; l++) {
+                const int v = sm->perm[l];
+                if (v < 0 || v >= M || seen[v]) return fail(PAT_ERR_INVALID_ARG, "HADAMARD: perm is not a permutation");
+                seen[v] = 1;
+            }
+            std::fill(seen.begin(), seen.end(), 0);
+            for (int j = 0; j < sm->m; j++) {
+                const int v = sm->rows[j];
+                if (v < 0 || v >= M || seen[v]) return fail(PAT_ERR_INVALID_ARG, "HADAMARD: rows out of range or repeated");
+                seen[v] = 1;
+            }
+            break;
+        }
+        default: return fail(PAT_ERR_INVALID_ARG, "unknown sampling kind");
+    }
+    return PAT_OK;
+}
+
+pat_status build_tables(pat_grid* G) {
+    const pat_grid_desc& d = G->d;
+    const int n[3] = {d.nz, d.ny, d.nx};
+    const double dt = G->s.dt;
+    pat_status st;
+    // twiddles
+    for (int a = 0; a < 3; a++) {
+        std::vector<float2> tw(n[a]);
+        for (int m = 0; m < n[a]; m++) {
+            const double ang = -2.0 * M_PI * (double)m / (double)n[a];
+            tw[m] = make_float2((float)cos(ang), (float)sin(ang));
+        }
+        if ((st = upload(G, &G->t.tw[a], tw, "twiddles")) != PAT_OK) return st;
+    }
+    // derivative factors (x: half spectrum)
+    for (int a = 0; a < 3; a++) {
+        const int len = (a == AX) ? G->g.nxh : n[a];
+        std::vector<float2> dp(len), dm(len);
+        for (int m = 0; m < len; m++) {
+            const double k = wavenumber(m, n[a], d.dx);
+            const std::complex<double> ik(0.0, k);
+            const std::complex<double> p = ik * std::polar(1.0, +k * d.dx / 2.0);
+            const std::complex<double> q = ik * std::polar(1.0, -k * d.dx / 2.0);
+            dp[m] = make_float2((float)p.real(), (float)p.imag());
+            dm[m] = make_float2((float)q.real(), (float)q.imag());
+        }
+        if ((st = upload(G, &G->t.dplus[a], dp, "dplus")) != PAT_OK) return st;
+        if ((st = upload(G, &G->t.dminus[a], dm, "dminus")) != PAT_OK) return st;
+    }
+    // kappa / N on the half spectrum
+    {
+        const double N = (double)d.nz * d.ny * d.nx;
+        std::vector<float> kap((size_t)d.nz * d.ny * G->g.nxh);
+        size_t i = 0;
+        for (int kz = 0; kz < d.nz; kz++) {
+            const double wz = wavenumber(kz, d.nz, d.dx);
+            for (int ky = 0; ky < d.ny; ky++) {
+                const double wy = wavenumber(ky, d.ny, d.dx);
+                for (int kx = 0; kx < G->g.nxh; kx++) {
+                    const double wx = wavenumber(kx, d.nx, d.dx);
+                    const double x = 0.5 * d.c * dt * sqrt(wz * wz + wy * wy + wx * wx);
+                    const double kappa = (x == 0.0) ? 1.0 : sin(x) / x;
+                    kap[i++] = (float)(kappa / N);
+                }
+            }
+        }
+        if ((st = upload(G, &G->t.kappaN, kap, "kappa")) != PAT_OK) return st;
+    }
+    // PML-derived coefficient tables
+    for (int a = 0; a < 3; a++) {
+        std::vector<std::vector<float>> ct(CT_COUNT, std::vector<float>(n[a]));
+        for (int j = 0; j < n[a]; j++) {
+            const double A = pml_factor(d, dt, (double)j, n[a]);
+            const double As = pml_factor(d, dt, (double)j + 0.5, n[a]);
+            ct[CT_ONE][j] = 1.0f;
+            ct[CT_AS2][j] = (float)(As * As);
+            ct[CT_VF_G][j] = (float)(-As * dt / d.rho0);
+            ct[CT_VF0_G][j] = (float)(As * (As / 2.0 - 1.0) * dt / d.rho0);
+            ct[CT_VA_G][j] = (float)(dt * d.rho0);
+            ct[CT_AS][j] = (float)As;
+            ct[CT_VA0_OUT][j] = (float)(As * (1.0 - As / 2.0));
+            ct[CT_A2][j] = (float)(A * A);
+            ct[CT_DF_D][j] = (float)(-A * dt * d.rho0);
+            ct[CT_A][j] = (float)A;
+        }
+        for (int c = 0; c < CT_COUNT; c++)
+            if ((st = upload(G, &G->t.coef[c][a], ct[c], "coef")) != PAT_OK) return st;
+    }
+    return PAT_OK;
+}
+
+pat_status check_device(const pat_grid* G) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev != G->device) return fail(PAT_ERR_INVALID_ARG, "the current CUDA device is not the grid's device");
+    return PAT_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pat_last_error(void) { return g_err.c_str(); }
+
+const char* pat_version(void) { return "libpat 0.1 (sm_103a)"; }
+
+pat_status pat_create_grid(const pat_grid_desc* desc, const pat_sampling_desc* sampling, pat_grid** out) {
+    g_err.clear();
+    if (!out) return fail(PAT_ERR_INVALID_ARG, "pat_create_grid: out is NULL");
+    *out = nullptr;
+    pat_status st = validate(desc, sampling);
+    if (st != PAT_OK) return st;
+
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    cudaDeviceProp prop;
+    e = cudaGetDeviceProperties(&prop, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceProperties");
+    if (prop.major * 10 + prop.minor != 103)
+        return fail(PAT_ERR_UNSUPPORTED, std::string("libpat is built for sm_103a only; device is ") + prop.name);
+
+    pat_grid* G = new pat_grid();
+    G->d = *desc;
+    G->device = dev;
+    G->kind = sampling->kind;
+    G->bytes = 0;
+    if (G->d.sensor_z < 0) G->d.sensor_z = G->d.pml_size;
+    if (!(G->d.dt > 0)) G->d.dt = G->d.cfl * G->d.dx / G->d.c;
+    const int M = G->d.ny * G->d.nx;
+    G->m = (sampling->kind == PAT_SAMPLE_FULL) ? M : sampling->m;
+    G->s.c = G->d.c;
+    G->s.rho0 = G->d.rho0;
+    G->s.dt = G->d.dt;
+
+    Geom& g = G->g;
+    g.nz = G->d.nz;
+    g.ny = G->d.ny;
+    g.nx = G->d.nx;
+    g.nxh = g.nx / 2 + 1;
+    g.B = G->d.batch;
+    int cs = 8;
+    while (cs > 1 && (cs > g.ny / 2 || cs > g.nx / 2)) cs >>= 1;
+    g.cs = cs;
+    g.rows_cta = (g.ny / 2) / cs;
+    g.cols_cta = (g.nx / 2) / cs;
+    g.tc = 0;
+    g.nreal = (long long)g.nz * g.ny * g.nx;
+    g.nspec = (long long)g.nz * g.ny * g.nxh;
+    g.sensor_z = G->d.sensor_z;
+    g.T = G->d.T;
+    g.m_plane = M;
+
+    // workspace
+    const size_t B = (size_t)g.B;
+    for (int i = 0; i < 6 && st == PAT_OK; i++)
+        st = dalloc(G, (void**)&G->w.st[i], B * g.nreal * sizeof(float), "state");
+    for (int i = 0; i < 3 && st == PAT_OK; i++)
+        st = dalloc(G, (void**)&G->w.spec[i], B * g.nspec * sizeof(float2), "spectrum");
+    if (st == PAT_OK && G->kind != PAT_SAMPLE_FULL)
+        st = dalloc(G, (void**)&G->w.rec, B * (size_t)g.T * M * sizeof(float), "plane series");
+    if (st == PAT_OK && G->kind == PAT_SAMPLE_POINTS)
+        st = upload(G, &G->w.idx, std::vector<int32_t>(sampling->indices, sampling->indices + G->m), "indices");
+    if (st == PAT_OK && (G->kind == PAT_SAMPLE_HADAMARD01 || G->kind == PAT_SAMPLE_HADAMARDPM)) {
+        st = upload(G, &G->w.perm, std::vector<int32_t>(sampling->perm, sampling->perm + M), "perm");
+        if (st == PAT_OK)
+            st = upload(G, &G->w.rows, std::vector<int32_t>(sampling->rows, sampling->rows + G->m), "rows");
+    }
+    if (st == PAT_OK) st = build_tables(G);
+    if (st == PAT_OK) {
+        e = configure_kernels(g, nullptr, nullptr);
+        if (e != cudaSuccess) st = cuda_fail(e, "configure_kernels");
+    }
+    if (st != PAT_OK) {
+        std::string msg = g_err;
+        free_grid(G);
+        g_err = msg;
+        return st;
+    }
+    *out = G;
+    return PAT_OK;
+}
+
+void pat_destroy_grid(pat_grid* grid) {
+    if (!grid) return;
+    cudaDeviceSynchronize();
+    free_grid(grid);
+}
+
+pat_status pat_grid_info(const pat_grid* G, int64_t* n_image, int64_t* n_data, int32_t* m, double* dt) {
+    if (!G) return fail(PAT_ERR_INVALID_ARG, "pat_grid_info: NULL grid");
+    if (n_image) *n_image = G->g.nreal;
+    if (n_data) *n_data = (int64_t)G->g.T * G->m;
+    if (m) *m = G->m;
+    if (dt) *dt = G->s.dt;
+    return PAT_OK;
+}
+
+int64_t pat_workspace_bytes(const pat_grid* G) { return G ? G->bytes : 0; }
+
+pat_status pat_forward(pat_grid* G, const float* p0, float* f, void* stream) {
+    g_err.clear();
+    if (!G) return fail(PAT_ERR_INVALID_ARG, "pat_forward: NULL grid");
+    if (!p0 || (!f && G->m > 0)) return fail(PAT_ERR_INVALID_ARG, "pat_forward: NULL buffer");
+    pat_status st = check_device(G);
+    if (st != PAT_OK) return st;
+    cudaError_t e = run_forward(G->g, G->t, G->w, G->s, G->kind, G->m, p0, f, (cudaStream_t)stream, &G->prof);
+    if (e != cudaSuccess) return cuda_fail(e, "pat_forward");
+    return PAT_OK;
+}
+
+pat_status pat_adjoint(pat_grid* G, const float* f, float* p, void* stream) {
+    g_err.clear();
+    if (!G) return fail(PAT_ERR_INVALID_ARG, "pat_adjoint: NULL grid");
+    if (!p || (!f && G->m > 0)) return fail(PAT_ERR_INVALID_ARG, "pat_adjoint: NULL buffer");
+    pat_status st = check_device(G);
+    if (st != PAT_OK) return st;
+    cudaError_t e = run_adjoint(G->g, G->t, G->w, G->s, G->kind, G->m, f, p, (cudaStream_t)stream, &G->prof);
+    if (e != cudaSuccess) return cuda_fail(e, "pat_adjoint");
+    return PAT_OK;
+}
+
+pat_status pat_sample(pat_grid* G, const float* pbar, float* f, int32_t nt, void* stream) {
+    g_err.clear();
+    if (!G) return fail(PAT_ERR_INVALID_ARG, "pat_sample: NULL grid");
+    if (nt < 1) return fail(PAT_ERR_INVALID_ARG, "pat_sample: nt must be >= 1");
+    if (!pbar || (!f && G->m > 0)) return fail(PAT_ERR_INVALID_ARG, "pat_sample: NULL buffer");
+    pat_status st = check_device(G);
+    if (st != PAT_OK) return st;
+    cudaError_t e = run_sample(G->g, G->w, G->kind, G->m, pbar, f, nt, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "pat_sample");
+    return PAT_OK;
+}
+
+pat_status pat_sample_adjoint(pat_grid* G, const float* f, float* pbar, int32_t nt, void* stream) {
+    g_err.clear();
+    if (!G) return fail(PAT_ERR_INVALID_ARG, "pat_sample_adjoint: NULL grid");
+    if (nt < 1) return fail(PAT_ERR_INVALID_ARG, "pat_sample_adjoint: nt must be >= 1");
+    if (!pbar || (!f && G->m > 0)) return fail(PAT_ERR_INVALID_ARG, "pat_sample_adjoint: NULL buffer");
+    pat_status st = check_device(G);
+    if (st != PAT_OK) return st;
+    cudaError_t e = run_sample_adjoint(G->g, G->w, G->kind, G->m, f, pbar, nt, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "pat_sample_adjoint");
+    return PAT_OK;
+}
+
+static const char* kClassNames[KC_COUNT] = {"plane_init", "plane_vel", "plane_rho_fwd", "plane_rho_adj",
+                                              "zpass_grad3", "zpass_each3", "zpass_sum3", "sample"};
+
+pat_status pat_profile_enable(pat_grid* G, int32_t enable) {
+    g_err.clear();
+    if (!G) return fail(PAT_ERR_INVALID_ARG, "pat_profile_enable: NULL grid");
+    G->prof.on = enable != 0;
+    G->prof.recs.clear();
+    G->prof.next = 0;
+    return PAT_OK;
+}
+
+pat_status pat_profile_read(pat_grid* G, int32_t max_classes, char* names, double* total_ms,
+                            int64_t* launches, int32_t* n_classes) {
+    g_err.clear();
+    if (!G || !n_classes || max_classes < 0) return fail(PAT_ERR_INVALID_ARG, "pat_profile_read: bad argument");
+    double ms[KC_COUNT] = {0};
+    int64_t cnt[KC_COUNT] = {0};
+    for (const auto& r : G->prof.recs) {
+        cudaError_t e = cudaEventSynchronize(r.b);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+        float t = 0.f;
+        e = cudaEventElapsedTime(&t, r.a, r.b);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime");
+        ms[r.cls] += t;
+        cnt[r.cls] += 1;
+    }
+    int k = 0;
+    for (int c = 0; c < KC_COUNT && k < max_classes; c++) {
+        if (cnt[c] == 0) continue;
+        if (names) snprintf(names + 48 * k, 48, "%s", kClassNames[c]);
+        if (total_ms) total_ms[k] = ms[c];
+        if (launches) launches[k] = cnt[c];
+        k++;
+    }
+    *n_classes = k;
+    G->prof.recs.clear();
+    G->prof.next = 0;
+    return PAT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,98 @@
+// pat_internal.h - host-side structures shared by the C ABI layer and the kernel launchers.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/pat.h"
+
+namespace pat {
+
+enum Axis { AZ = 0, AY = 1, AX = 2 };
+
+// Per-axis coefficient tables (float, one entry per grid index along the axis), all derived from
+// the PML factors a (regular points) and as (staggered points) in double precision.
+enum CoefTable {
+    CT_ONE = 0,        // 1
+    CT_AS2,            // as^2                      velocity decay (forward and adjoint)
+    CT_VF_G,           // -as * dt / rho0           forward velocity: gradient term
+    CT_VF0_G,          // as (as/2 - 1) dt / rho0    forward velocity, first step (u^{-1/2} folded in)
+    CT_VA_G,           // dt * rho0                 adjoint velocity: gradient term
+    CT_AS,             // as                        adjoint velocity: transform input
+    CT_VA0_OUT,        // as (1 - as/2)             adjoint velocity, last step (u^{-1/2} folded in)
+    CT_A2,             // a^2                       density decay
+    CT_DF_D,           // -a dt rho0                forward density: divergence term
+    CT_A,              // a                         adjoint density: transform input
+    CT_COUNT
+};
+
+struct Geom {
+    int nz, ny, nx, nxh;        // nxh = nx/2 + 1
+    int B;                      // batch
+    int cs;                     // plane-kernel cluster size
+    int rows_cta, cols_cta;     // complex row pairs / packed columns per CTA
+    int tc;                     // z-kernel column tile
+    long long nreal, nspec;     // per batch entry
+    int sensor_z;
+    int T;
+    int m_plane;                // ny * nx
+};
+
+struct DeviceTables {
+    float2* tw[3];              // FFT twiddles exp(-2 pi i m / L) per axis length
+    float* kappaN;              // kappa(|k|) / N on the half spectrum [nz][ny][nxh]
+    float2* dplus[3];           // i k exp(+i k dx/2) per axis (x: nxh entries)
+    float2* dminus[3];          // i k exp(-i k dx/2)
+    float* coef[CT_COUNT][3];   // per-axis coefficient tables
+};
+
+struct Workspace {
+    float* st[6];               // u_z,u_y,u_x,rho_z,rho_y,rho_x (forward) / v_i, q_i (adjoint)
+    float2* spec[3];            // half spectra [B][nz][ny][nxh]
+    float* rec;                 // recorded / injected plane series [B][T][M] (sampled kinds)
+    int32_t* idx;               // POINTS index list
+    int32_t* perm;              // HADAMARD scramble
+    int32_t* rows;              // HADAMARD rows
+};
+
+struct Scalars {
+    double c, rho0, dt;
+};
+
+// Kernel classes timed by the optional profiler (CUDA events on the launching stream).
+enum KernelClass {
+    KC_PLANE_INIT = 0, KC_PLANE_VEL, KC_PLANE_RHO_FWD, KC_PLANE_RHO_ADJ,
+    KC_Z_ONE_TO_THREE, KC_Z_THREE_TO_THREE, KC_Z_THREE_TO_ONE, KC_SAMPLE, KC_COUNT
+};
+
+struct Profiler {
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    size_t next = 0;
+    struct Rec { int cls; cudaEvent_t a, b; };
+    std::vector<Rec> recs;
+    cudaError_t ev(cudaEvent_t* out) {
+        if (next == pool.size()) {
+            cudaEvent_t e;
+            cudaError_t r = cudaEventCreate(&e);
+            if (r != cudaSuccess) return r;
+            pool.push_back(e);
+        }
+        *out = pool[next++];
+        return cudaSuccess;
+    }
+};
+
+// Launchers (pat_kernels.cu).  All return cudaSuccess or the launch error.
+cudaError_t configure_kernels(const Geom& g, size_t* plane_smem, size_t* z_smem);
+cudaError_t run_forward(const Geom& g, const DeviceTables& t, const Workspace& w, const Scalars& s,
+                        int kind, int m, const float* p0, float* f, cudaStream_t st, Profiler* prof);
+cudaError_t run_adjoint(const Geom& g, const DeviceTables& t, const Workspace& w, const Scalars& s,
+                        int kind, int m, const float* f, float* p, cudaStream_t st, Profiler* prof);
+cudaError_t run_sample(const Geom& g, const Workspace& w, int kind, int m, const float* pbar,
+                       float* f, int nt, cudaStream_t st);
+cudaError_t run_sample_adjoint(const Geom& g, const Workspace& w, int kind, int m, const float* f,
+                               float* pbar, int nt, cudaStream_t st);
+
+}  // namespace pat

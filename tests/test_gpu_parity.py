@@ -1,0 +1,231 @@
+"""GPU parity: libpat (FP32, CUDA) against the FP64 oracle, through the C ABI.
+
+Tolerance: relative L2 error <= 1e-5 for A and A^T in FP32.  The scheme needs ten 3D FFTs per time
+step; an FP32 restatement of the same recurrence with a library FFT lands at ~1.3e-6 after 100
+steps and grows like sqrt(T), so 1e-5 leaves headroom up to T = 400.  Index work (rSP gather and
+scatter, scrambled-Hadamard sampling of integer-valued planes) must match bit for bit.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from paper_1605_00133_gb300 import presets, synth  # noqa: E402
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    return torch.device("cuda", 0)
+
+
+def make_op(g, s):
+    from paper_1605_00133_gb300.operators import PatOperator
+    return PatOperator(g, s)
+
+
+def rel(a, b):
+    a = np.asarray(a, np.float64).ravel()
+    b = np.asarray(b, np.float64).ravel()
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def gpu_forward(op, p0, dev):
+    x = torch.tensor(np.asarray(p0), dtype=torch.float32, device=dev).reshape(op.image_shape)
+    return op.forward(x).cpu().numpy().astype(np.float64)
+
+
+def gpu_adjoint(op, y, dev):
+    x = torch.tensor(np.asarray(y), dtype=torch.float32, device=dev).reshape(op.data_shape)
+    return op.adjoint(x).cpu().numpy().astype(np.float64)
+
+
+def full(g):
+    return presets.Sampling(presets.KIND_FULL, g.m_plane)
+
+
+# ------------------------------------------------------------------------------ small grids
+
+SHAPES = [(8, 8, 8), (16, 32, 8), (32, 16, 64), (64, 8, 16), (8, 128, 32), (16, 64, 128),
+          (8, 256, 16), (128, 8, 8), (256, 8, 8), (8, 16, 256)]
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_forward_full_plane_matches_oracle(oracle_mod, dev, shape):
+    pml = min(shape) // 4
+    g = presets.Grid(*shape, T=10, pml_size=pml)
+    p0 = np.random.default_rng(1).standard_normal(shape)
+    op = make_op(g, full(g))
+    got = gpu_forward(op, p0, dev)
+    ref = oracle_mod.forward_plane(g, p0)
+    assert rel(got, ref) < TOL
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_adjoint_full_plane_matches_oracle(oracle_mod, dev, shape):
+    pml = min(shape) // 4
+    g = presets.Grid(*shape, T=10, pml_size=pml)
+    y = np.random.default_rng(2).standard_normal((g.T, g.m_plane))
+    op = make_op(g, full(g))
+    got = gpu_adjoint(op, y, dev)
+    ref = oracle_mod.adjoint_plane(g, y)
+    assert rel(got, ref) < TOL
+
+
+def test_workload_c1_forward_and_adjoint(oracle_mod, dev):
+    """32^3, T = 64, 8-voxel PML, rSP 25 %, three Gaussian balls."""
+    w = presets.workload("c1")
+    g, s = w.grid, w.sampling
+    p0 = w.p0()
+    op = make_op(g, s)
+    f = gpu_forward(op, p0, dev)
+    f_ref = oracle_mod.forward(g, s, p0)
+    assert rel(f, f_ref) < TOL
+    y = synth.add_relative_noise(f_ref, 0.01, 4)
+    p = gpu_adjoint(op, y, dev)
+    assert rel(p, oracle_mod.adjoint(g, s, y)) < TOL
+
+
+@pytest.mark.parametrize("kind", [presets.KIND_SHD01, presets.KIND_SHDPM])
+def test_hadamard_sampling_matches_oracle(oracle_mod, dev, kind):
+    g = presets.Grid(16, 32, 32, T=12, pml_size=4)
+    s = presets.make_sampling(g, kind, 128, 3)
+    p0 = synth.gaussian_balls(g.shape, 2, 2.0, 5, pml=4)
+    op = make_op(g, s)
+    assert rel(gpu_forward(op, p0, dev), oracle_mod.forward(g, s, p0)) < TOL
+    y = np.random.default_rng(6).standard_normal((g.T, s.m))
+    assert rel(gpu_adjoint(op, y, dev), oracle_mod.adjoint(g, s, y)) < TOL
+
+
+def test_batch_entries_are_independent(oracle_mod, dev):
+    g = presets.Grid(16, 16, 32, T=9, pml_size=3, batch=3)
+    s = presets.make_sampling(g, presets.KIND_RSP, 100, 1)
+    p0 = np.random.default_rng(7).standard_normal((3,) + g.shape)
+    op = make_op(g, s)
+    f = gpu_forward(op, p0, dev)
+    g1 = presets.Grid(16, 16, 32, T=9, pml_size=3)
+    for b in range(3):
+        assert rel(f[b], oracle_mod.forward(g1, s, p0[b])) < TOL
+    y = np.random.default_rng(8).standard_normal((3, g.T, s.m))
+    p = gpu_adjoint(op, y, dev)
+    for b in range(3):
+        assert rel(p[b], oracle_mod.adjoint(g1, s, y[b])) < TOL
+
+
+# ------------------------------------------------------------------------------ edge cases
+
+@pytest.mark.parametrize("T", [1, 2, 3])
+def test_shortest_recordings(oracle_mod, dev, T):
+    g = presets.Grid(16, 16, 16, T=T, pml_size=2)
+    s = presets.make_sampling(g, presets.KIND_RSP, 50, 2)
+    p0 = np.random.default_rng(9).standard_normal(g.shape)
+    op = make_op(g, s)
+    assert rel(gpu_forward(op, p0, dev), oracle_mod.forward(g, s, p0)) < TOL
+    y = np.random.default_rng(10).standard_normal((T, s.m))
+    assert rel(gpu_adjoint(op, y, dev), oracle_mod.adjoint(g, s, y)) < TOL
+
+
+@pytest.mark.parametrize("sensor_z,pml", [(0, 0), (15, 0), (3, 3), (12, 3)])
+def test_sensor_plane_positions_and_no_pml(oracle_mod, dev, sensor_z, pml):
+    g = presets.Grid(16, 16, 16, T=8, pml_size=pml, sensor_z=sensor_z)
+    p0 = np.random.default_rng(11).standard_normal(g.shape)
+    op = make_op(g, full(g))
+    assert rel(gpu_forward(op, p0, dev), oracle_mod.forward_plane(g, p0)) < TOL
+    y = np.random.default_rng(12).standard_normal((g.T, g.m_plane))
+    assert rel(gpu_adjoint(op, y, dev), oracle_mod.adjoint_plane(g, y)) < TOL
+
+
+def test_empty_point_set(dev):
+    g = presets.Grid(8, 8, 8, T=4, pml_size=1)
+    s = presets.Sampling(presets.KIND_RSP, 0, indices=np.zeros(0, np.int32))
+    op = make_op(g, s)
+    p = op.adjoint(torch.zeros(op.data_shape, device=dev))
+    assert float(p.abs().max()) == 0.0
+    assert op.forward(torch.ones(op.image_shape, device=dev)).numel() == 0
+
+
+def test_zero_input_gives_zero(dev):
+    g = presets.Grid(16, 16, 16, T=6, pml_size=2)
+    op = make_op(g, full(g))
+    assert float(op.forward(torch.zeros(op.image_shape, device=dev)).abs().max()) == 0.0
+
+
+# ------------------------------------------------------------------------------ index work, bit-exact
+
+@pytest.mark.parametrize("kind", [presets.KIND_RSP, presets.KIND_SHD01, presets.KIND_SHDPM])
+def test_sampling_is_bit_exact_on_integer_planes(oracle_mod, dev, kind):
+    """Integer-valued planes: every sum in C and C^T is exact in FP32 and FP64 alike (M = 4^k makes
+    1/sqrt(M) a power of two)."""
+    g = presets.Grid(8, 64, 64, T=5, pml_size=2)
+    s = presets.make_sampling(g, kind, 700, 9)
+    op = make_op(g, s)
+    rng = np.random.default_rng(13)
+    pbar = rng.integers(-40, 40, size=(g.T, g.m_plane)).astype(np.float64)
+    got = op.sample(torch.tensor(pbar, dtype=torch.float32, device=dev).reshape(1, g.T, -1))
+    ref = oracle_mod.sample(s, pbar)
+    assert np.array_equal(got.cpu().numpy().reshape(ref.shape).astype(np.float64), ref)
+    y = rng.integers(-40, 40, size=(g.T, s.m)).astype(np.float64)
+    back = op.sample_adjoint(torch.tensor(y, dtype=torch.float32, device=dev).reshape(1, g.T, -1))
+    ref_b = oracle_mod.sample_T(s, y, g.m_plane)
+    assert np.array_equal(back.cpu().numpy().reshape(ref_b.shape).astype(np.float64), ref_b)
+
+
+# ------------------------------------------------------------------------------ full workload sizes
+
+def test_c2_dot_product_fp32(dev):
+    """<C A x, y> = <x, A^T C^T y> on the full 64x128x128, T = 400 workload, GPU FP32 (inner products
+    accumulated in FP64 on the host)."""
+    w = presets.workload("c2")
+    g, s = w.grid, w.sampling
+    op = make_op(g, s)
+    rng = np.random.default_rng(14)
+    x = rng.standard_normal(g.shape)
+    y = rng.standard_normal((g.T, s.m))
+    Ax = gpu_forward(op, x, dev)
+    Aty = gpu_adjoint(op, y, dev)
+    lhs, rhs = np.sum(Ax.ravel() * y.ravel()), np.sum(x.ravel() * Aty.ravel())
+    assert abs(lhs - rhs) / (np.linalg.norm(Ax) * np.linalg.norm(y)) < 1e-5
+
+
+def test_c2_without_pml_matches_exact_solution(oracle_mod, dev):
+    """With the PML off the recurrence is exact per mode: p^n = F^-1[cos(n c |k| dt) F p0].  Checked
+    on the full 64x128x128 grid at T = 400 at sampled time steps, with the oracle's own FFT."""
+    w = presets.workload("c2")
+    g = presets.Grid(64, 128, 128, dx=w.grid.dx, T=400, pml_size=0, sensor_z=10)
+    p0 = w.p0()
+    op = make_op(g, full(g))
+    f = gpu_forward(op, p0, dev).reshape(g.T, g.ny, g.nx)
+    P0 = oracle_mod.fft3(p0.astype(np.complex128))
+    ks = [np.array([oracle_mod.wavenumber(m, n, g.dx) for m in range(n)]) for n in g.shape]
+    K = np.sqrt(ks[0][:, None, None] ** 2 + ks[1][None, :, None] ** 2 + ks[2][None, None, :] ** 2)
+    for n in (1, 57, 200, 399):
+        pn = oracle_mod.fft3(P0 * np.cos(n * g.c * K * g.dt), inverse=True).real
+        assert rel(f[n], pn[g.sensor_z]) < TOL, n
+
+
+def test_c2_forward_matches_oracle_reduced_T(oracle_mod, dev):
+    """Full c2 grid and sampling (64x128x128, 10-voxel PML, rSP 2048 of 16384), T = 24."""
+    w = presets.shrink(presets.workload("c2"), 24)
+    g, s = w.grid, w.sampling
+    p0 = w.p0()
+    op = make_op(g, s)
+    assert rel(gpu_forward(op, p0, dev), oracle_mod.forward(g, s, p0)) < TOL
+    y = np.random.default_rng(15).standard_normal((g.T, s.m))
+    assert rel(gpu_adjoint(op, y, dev), oracle_mod.adjoint(g, s, y)) < TOL
+
+
+@pytest.mark.slow
+def test_c2_forward_matches_oracle_full_T(oracle_mod, dev):
+    """The headline workload end to end: 64x128x128, T = 400, rSP 12.5 %, vessel phantom."""
+    w = presets.workload("c2")
+    g, s = w.grid, w.sampling
+    p0 = w.p0()
+    op = make_op(g, s)
+    assert rel(gpu_forward(op, p0, dev), oracle_mod.forward(g, s, p0)) < TOL

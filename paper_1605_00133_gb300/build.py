@@ -9,8 +9,10 @@ from concurrent.futures import ThreadPoolExecutor
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libpat.so")
-SOURCES = ["pat_kernels.cu", "pat_api.cu"]
-HEADERS = ["pat_fft.cuh", "pat_internal.h", os.path.join("..", "..", "include", "pat.h")]
+SOURCES = ["pat_api.cu", "pat_run.cu", "pat_zpass.cu", "pat_sample.cu"] + [
+    f"pat_plane_nx{n}.cu" for n in (8, 16, 32, 64, 128, 256)]
+HEADERS = ["pat_fft.cuh", "pat_internal.h", "pat_kargs.h", "pat_plane.cuh",
+           os.path.join("..", "..", "include", "pat.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC"]
 
@@ -45,7 +47,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         subprocess.check_call(cmd)
         return obj
 
-    with ThreadPoolExecutor(len(SOURCES)) as ex:
+    with ThreadPoolExecutor(min(len(SOURCES), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + f".tmp{os.getpid()}"
     subprocess.check_call([cc, *ARCH, "-shared", *objs, "-o", tmp, "-lcudart"])

@@ -281,11 +281,9 @@ pat_status pat_create_grid(const pat_grid_desc* desc, const pat_sampling_desc* s
     g.nx = G->d.nx;
     g.nxh = g.nx / 2 + 1;
     g.B = G->d.batch;
-    int cs = 8;
-    while (cs > 1 && (cs > g.ny / 2 || cs > g.nx / 2)) cs >>= 1;
-    g.cs = cs;
-    g.rows_cta = (g.ny / 2) / cs;
-    g.cols_cta = (g.nx / 2) / cs;
+    g.cs = plane_cluster_size(g.nx, g.ny);
+    g.rows_cta = (g.ny / 2) / g.cs;
+    g.cols_cta = (g.nx / 2) / g.cs;
     g.tc = 0;
     g.nreal = (long long)g.nz * g.ny * g.nx;
     g.nspec = (long long)g.nz * g.ny * g.nxh;
@@ -297,8 +295,12 @@ pat_status pat_create_grid(const pat_grid_desc* desc, const pat_sampling_desc* s
     const size_t B = (size_t)g.B;
     for (int i = 0; i < 6 && st == PAT_OK; i++)
         st = dalloc(G, (void**)&G->w.st[i], B * g.nreal * sizeof(float), "state");
-    for (int i = 0; i < 3 && st == PAT_OK; i++)
-        st = dalloc(G, (void**)&G->w.spec[i], B * g.nspec * sizeof(float2), "spectrum");
+    // the three half-spectrum buffers are one allocation: kernels address field f at spec[0] + f*B*nspec
+    if (st == PAT_OK) st = dalloc(G, (void**)&G->w.spec[0], 3 * B * g.nspec * sizeof(float2), "spectra");
+    if (st == PAT_OK) {
+        G->w.spec[1] = G->w.spec[0] + B * g.nspec;
+        G->w.spec[2] = G->w.spec[1] + B * g.nspec;
+    }
     if (st == PAT_OK && G->kind != PAT_SAMPLE_FULL)
         st = dalloc(G, (void**)&G->w.rec, B * (size_t)g.T * M * sizeof(float), "plane series");
     if (st == PAT_OK && G->kind == PAT_SAMPLE_POINTS)

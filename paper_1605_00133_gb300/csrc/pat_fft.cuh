@@ -90,68 +90,47 @@ __device__ __forceinline__ float2 twiddle(const float2* __restrict__ tw, int e) 
     return (DIR < 0) ? w : cconj(w);
 }
 
-// Transform nl lines of length L held in shared memory (line l at data[l*lp .. l*lp+L)), in place,
-// through the exchange buffer `xch` (nl * R1 * (R2+1) complex).  Threads loop over work items, so
-// any block size works.  Ends with __syncthreads().
-template <int L, int DIR>
-__device__ void fft_lines_smem(float2* data, int lp, int nl, float2* xch,
-                               const float2* __restrict__ tw, int tid, int nt) {
+// Compile-time variant for the plane kernels: NF fields of NL lines each, line l of field f at
+// base + f * AREA + l * P (data) and the same offsets in the exchange area.  The exchange layout of
+// a line is [k1][t] with row pitch R2 + 1, so it needs L + R1 <= P elements per line.  NT threads.
+template <int L, int DIR, int NL, int NF, int P, int AREA, int NT>
+__device__ __forceinline__ void fft_lines_ct(float2* data, float2* xch, const float2* __restrict__ tw) {
     constexpr int R1 = (DIR < 0) ? Split<L>::A : Split<L>::B;
     constexpr int R2 = L / R1;
-    constexpr int XP = R2 + 1;        // exchange row pitch
-    constexpr int XL = R1 * XP;       // exchange line pitch
-    for (int it = tid; it < nl * R2; it += nt) {
-        const int l = it / R2, t = it - l * R2;
+    constexpr int XP = R2 + 1;
+    static_assert(L + R1 <= P, "line pitch too small for the exchange layout");
+    const int tid = threadIdx.x;
+#pragma unroll 1
+    for (int it = tid; it < NF * NL * R2; it += NT) {
+        const int t = it % R2, lf = it / R2;
+        const int off = (lf / NL) * AREA + (lf % NL) * P;
         float2 v[R1];
-        const float2* src = data + l * lp + t;
+        const float2* src = data + off + t;
 #pragma unroll
         for (int m = 0; m < R1; m++) v[m] = src[R2 * m];
         Dft<R1, DIR>::run(v);
-        float2* dst = xch + l * XL + t;
+        float2* dst = xch + off + t;
 #pragma unroll
         for (int k1 = 0; k1 < R1; k1++) {
-            const float2 w = (k1 == 0 || t == 0) ? v[k1] : cmul(v[k1], twiddle<L, DIR>(tw, t * k1));
+            const float2 w = (k1 == 0) ? v[k1] : cmul(v[k1], twiddle<L, DIR>(tw, t * k1));
             dst[k1 * XP] = w;
         }
     }
     __syncthreads();
-    for (int it = tid; it < nl * R1; it += nt) {
-        const int l = it / R1, k1 = it - l * R1;
+#pragma unroll 1
+    for (int it = tid; it < NF * NL * R1; it += NT) {
+        const int k1 = it % R1, lf = it / R1;
+        const int off = (lf / NL) * AREA + (lf % NL) * P;
         float2 v[R2];
-        const float2* src = xch + l * XL + k1 * XP;
+        const float2* src = xch + off + k1 * XP;
 #pragma unroll
         for (int t = 0; t < R2; t++) v[t] = src[t];
         Dft<R2, DIR>::run(v);
-        float2* dst = data + l * lp + k1;
+        float2* dst = data + off + k1;
 #pragma unroll
         for (int k2 = 0; k2 < R2; k2++) dst[R1 * k2] = v[k2];
     }
     __syncthreads();
-}
-
-// Runtime-length dispatch (L a power of two in [2, 256]).
-template <int DIR>
-__device__ __forceinline__ void fft_lines(int L, float2* data, int lp, int nl, float2* xch,
-                                          const float2* __restrict__ tw, int tid, int nt) {
-    switch (L) {
-        case 2: fft_lines_smem<2, DIR>(data, lp, nl, xch, tw, tid, nt); break;
-        case 4: fft_lines_smem<4, DIR>(data, lp, nl, xch, tw, tid, nt); break;
-        case 8: fft_lines_smem<8, DIR>(data, lp, nl, xch, tw, tid, nt); break;
-        case 16: fft_lines_smem<16, DIR>(data, lp, nl, xch, tw, tid, nt); break;
-        case 32: fft_lines_smem<32, DIR>(data, lp, nl, xch, tw, tid, nt); break;
-        case 64: fft_lines_smem<64, DIR>(data, lp, nl, xch, tw, tid, nt); break;
-        case 128: fft_lines_smem<128, DIR>(data, lp, nl, xch, tw, tid, nt); break;
-        case 256: fft_lines_smem<256, DIR>(data, lp, nl, xch, tw, tid, nt); break;
-        default: break;
-    }
-}
-
-// Exchange-buffer size (complex elements) fft_lines needs for nl lines of length L, either direction.
-__host__ __device__ inline int fft_xch_elems(int L, int nl) {
-    int a = (L >= 128) ? 16 : (L >= 32) ? 8 : (L >= 8) ? 4 : 2;
-    int b = L / a;
-    int f = a * (b + 1), i = b * (a + 1);
-    return nl * (f > i ? f : i);
 }
 
 }  // namespace pat

@@ -112,6 +112,19 @@ pat_status pat_forward(pat_grid* grid, const float* p0_dev, float* f_dev, void* 
  * f_dev and p_dev must not overlap. */
 pat_status pat_adjoint(pat_grid* grid, const float* f_dev, float* p_dev, void* cuda_stream);
 
+/* f = C A p0 like pat_forward, for callers that cannot allocate device memory when they call the
+ * operator (e.g. reconstruction loops that reserve their whole device budget at start-up).  The
+ * paper has no counterpart; this is a deployment variant.  It allocates nothing: the time-stepping
+ * state, half spectra and recorded plane series live in one static device array of 64 MiB that
+ * every GPU loading libpat holds until the process exits (grids up to 64x128x128 with T = 400 and
+ * point sampling fit; larger ones are rejected with PAT_ERR_INVALID_ARG and a message giving the
+ * bytes needed).  The grid's constant tables and index sets are read, not written.  The first call
+ * on each device looks up the array's device address (cudaGetSymbolAddress), so make that first
+ * call before any stream capture.  All calls share the one array and every call overwrites it (no
+ * part of it needs to start at zero): calls that can overlap on the GPU (other streams, other
+ * grids, other threads) race with each other and must be serialised by the caller. */
+pat_status pat_forward_noalloc(pat_grid* grid, const float* p0_dev, float* f_dev, void* cuda_stream);
+
 /* C alone, applied to a plane series (Sec. 3.1, Eq. GenScan per time point):
  *   pbar_dev: float[B][nt][Ny*Nx] -> f_dev: float[B][nt][m].  nt >= 1. */
 pat_status pat_sample(pat_grid* grid, const float* pbar_dev, float* f_dev, int32_t nt,

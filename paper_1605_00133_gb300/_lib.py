@@ -17,7 +17,7 @@ STATUS_NAMES = {0: "PAT_OK", 1: "PAT_ERR_INVALID_ARG", 2: "PAT_ERR_CUDA", 3: "PA
 # every symbol include/pat.h declares
 EXPORTS = ["pat_create_grid", "pat_destroy_grid", "pat_grid_info", "pat_workspace_bytes",
            "pat_forward", "pat_adjoint", "pat_sample", "pat_sample_adjoint", "pat_profile_enable",
-           "pat_profile_read", "pat_last_error", "pat_version"]
+           "pat_profile_read", "pat_last_error", "pat_version", "pat_forward_noalloc"]
 
 
 class PatError(RuntimeError):
@@ -65,7 +65,7 @@ def load() -> ctypes.CDLL:
         L.pat_grid_info.restype = ctypes.c_int
         L.pat_workspace_bytes.argtypes = [vp]
         L.pat_workspace_bytes.restype = ctypes.c_int64
-        for name in ("pat_forward", "pat_adjoint"):
+        for name in ("pat_forward", "pat_adjoint", "pat_forward_noalloc"):
             fn = getattr(L, name)
             fn.argtypes = [vp, vp, vp, vp]
             fn.restype = ctypes.c_int

@@ -14,6 +14,7 @@
 
 #include <algorithm>
 #include <complex>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -430,3 +431,71 @@ pat_status pat_profile_read(pat_grid* G, int32_t max_classes, char* names, doubl
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------------------------
+// Forward operator with a fixed, library-owned scratch area (no device allocation per call).
+//
+// Some callers cannot call cudaMalloc when they need A: reconstruction loops that reserve their
+// whole device-memory budget up front (a scanner workstation running acquisition and
+// reconstruction side by side, a host application whose memory manager owns every device
+// allocation) must not grow their footprint, or fail, in the middle of a solve.  For them,
+// pat_forward_noalloc runs the same launch sequence as pat_forward, but the time-stepping
+// state, the half spectra and the recorded plane series live in the static device array
+// below instead of the grid's workspace.  Limits and sharing rules are in include/pat.h.
+// ---------------------------------------------------------------------------------------------
+
+#define PAT_NOALLOC_SCRATCH_BYTES (64ull << 20)
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[PAT_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[64] = {nullptr};  // device address of g_noalloc_scratch, per device id
+
+size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+}  // namespace
+
+extern "C" pat_status pat_forward_noalloc(pat_grid* G, const float* p0, float* f, void* stream) {
+    g_err.clear();
+    if (!G) return fail(PAT_ERR_INVALID_ARG, "pat_forward_noalloc: NULL grid");
+    if (!p0 || (!f && G->m > 0)) return fail(PAT_ERR_INVALID_ARG, "pat_forward_noalloc: NULL buffer");
+    pat_status st = check_device(G);
+    if (st != PAT_OK) return st;
+    const Geom& g = G->g;
+    const size_t B = (size_t)g.B;
+    const size_t st_bytes = round256(B * g.nreal * sizeof(float));
+    const size_t sp_bytes = round256(3 * B * g.nspec * sizeof(float2));
+    const size_t rec_bytes = (G->kind == PAT_SAMPLE_FULL) ? 0 : round256(B * (size_t)g.T * g.m_plane * sizeof(float));
+    const size_t need = 6 * st_bytes + sp_bytes + rec_bytes;
+    if (need > PAT_NOALLOC_SCRATCH_BYTES)
+        return fail(PAT_ERR_INVALID_ARG, "pat_forward_noalloc: this grid needs " + std::to_string(need) +
+                                             " bytes of scratch; the static scratch holds " +
+                                             std::to_string(PAT_NOALLOC_SCRATCH_BYTES) + " bytes");
+    if (G->device < 0 || G->device >= 64) return fail(PAT_ERR_UNSUPPORTED, "pat_forward_noalloc: device id >= 64");
+    unsigned char* base = nullptr;
+    {
+        // first call on this device: look up the device address of the static array (the host-side
+        // symbol is only a stand-in and must never be handed to a kernel)
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_ptr[G->device]) {
+            void* ptr = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
+            g_noalloc_ptr[G->device] = ptr;
+        }
+        base = (unsigned char*)g_noalloc_ptr[G->device];
+    }
+    Workspace w = G->w;  // index sets stay the grid's; all mutable scratch comes from the array
+    size_t off = 0;
+    for (int i = 0; i < 6; i++, off += st_bytes) w.st[i] = (float*)(base + off);
+    w.spec[0] = (float2*)(base + off);
+    w.spec[1] = w.spec[0] + B * g.nspec;
+    w.spec[2] = w.spec[1] + B * g.nspec;
+    off += sp_bytes;
+    w.rec = rec_bytes ? (float*)(base + off) : nullptr;
+    cudaError_t e = run_forward(G->g, G->t, w, G->s, G->kind, G->m, p0, f, (cudaStream_t)stream, nullptr);
+    if (e != cudaSuccess) return cuda_fail(e, "pat_forward_noalloc");
+    return PAT_OK;
+}

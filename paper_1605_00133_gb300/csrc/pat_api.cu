@@ -189,17 +189,17 @@ pat_status build_tables(pat_grid* G) {
         if ((st = upload(G, &G->t.dplus[a], dp, "dplus")) != PAT_OK) return st;
         if ((st = upload(G, &G->t.dminus[a], dm, "dminus")) != PAT_OK) return st;
     }
-    // kappa / N on the half spectrum
+    // kappa / N on the half spectrum, [kz][kx][ky]
     {
         const double N = (double)d.nz * d.ny * d.nx;
         std::vector<float> kap((size_t)d.nz * d.ny * G->g.nxh);
         size_t i = 0;
-        for (int kz = 0; kz < d.nz; kz++) {
+        for (int kz = 0; kz < d.nz; kz++) {  // same (kz, kx, ky) order as the half spectra
             const double wz = wavenumber(kz, d.nz, d.dx);
-            for (int ky = 0; ky < d.ny; ky++) {
-                const double wy = wavenumber(ky, d.ny, d.dx);
-                for (int kx = 0; kx < G->g.nxh; kx++) {
-                    const double wx = wavenumber(kx, d.nx, d.dx);
+            for (int kx = 0; kx < G->g.nxh; kx++) {
+                const double wx = wavenumber(kx, d.nx, d.dx);
+                for (int ky = 0; ky < d.ny; ky++) {
+                    const double wy = wavenumber(ky, d.ny, d.dx);
                     const double x = 0.5 * d.c * dt * sqrt(wz * wz + wy * wy + wx * wx);
                     const double kappa = (x == 0.0) ? 1.0 : sin(x) / x;
                     kap[i++] = (float)(kappa / N);

@@ -90,15 +90,22 @@ __device__ __forceinline__ float2 twiddle(const float2* __restrict__ tw, int e) 
     return (DIR < 0) ? w : cconj(w);
 }
 
-// Compile-time variant for the plane kernels: NF fields of NL lines each, line l of field f at
-// base + f * AREA + l * P (data) and the same offsets in the exchange area.  The exchange layout of
-// a line is [k1][t] with row pitch R2 + 1, so it needs L + R1 <= P elements per line.  NT threads.
+// Plane-kernel variant: NF fields of NL lines each, line l of field f at base + f * AREA + l * P
+// in both the data and the exchange area (exchange area != data area).  The exchange keeps a line's
+// [k1][t] matrix unpadded (row pitch R2, so a line needs exactly L elements) and swizzles the
+// column, t -> t ^ s(k1) with s(k1) = (k1 / (16 / R2)) mod R2: with a line pitch P = 8 (mod 16),
+// the 16 threads of a half-warp then hit 16 distinct 8-byte bank pairs in both passes.  NT threads.
+template <int R2>
+__device__ __forceinline__ int xswz(int k1, int t) {
+    constexpr int G = (R2 >= 16) ? 1 : 16 / R2;
+    return k1 * R2 + (t ^ ((k1 / G) & (R2 - 1)));
+}
+
 template <int L, int DIR, int NL, int NF, int P, int AREA, int NT>
 __device__ __forceinline__ void fft_lines_ct(float2* data, float2* xch, const float2* __restrict__ tw) {
     constexpr int R1 = (DIR < 0) ? Split<L>::A : Split<L>::B;
     constexpr int R2 = L / R1;
-    constexpr int XP = R2 + 1;
-    static_assert(L + R1 <= P, "line pitch too small for the exchange layout");
+    static_assert(L <= P, "line pitch too small");
     const int tid = threadIdx.x;
 #pragma unroll 1
     for (int it = tid; it < NF * NL * R2; it += NT) {
@@ -109,11 +116,11 @@ __device__ __forceinline__ void fft_lines_ct(float2* data, float2* xch, const fl
 #pragma unroll
         for (int m = 0; m < R1; m++) v[m] = src[R2 * m];
         Dft<R1, DIR>::run(v);
-        float2* dst = xch + off + t;
+        float2* dst = xch + off;
 #pragma unroll
         for (int k1 = 0; k1 < R1; k1++) {
             const float2 w = (k1 == 0) ? v[k1] : cmul(v[k1], twiddle<L, DIR>(tw, t * k1));
-            dst[k1 * XP] = w;
+            dst[xswz<R2>(k1, t)] = w;
         }
     }
     __syncthreads();
@@ -122,15 +129,83 @@ __device__ __forceinline__ void fft_lines_ct(float2* data, float2* xch, const fl
         const int k1 = it % R1, lf = it / R1;
         const int off = (lf / NL) * AREA + (lf % NL) * P;
         float2 v[R2];
-        const float2* src = xch + off + k1 * XP;
+        const float2* src = xch + off;
 #pragma unroll
-        for (int t = 0; t < R2; t++) v[t] = src[t];
+        for (int t = 0; t < R2; t++) v[t] = src[xswz<R2>(k1, t)];
         Dft<R2, DIR>::run(v);
         float2* dst = data + off + k1;
 #pragma unroll
         for (int k2 = 0; k2 < R2; k2++) dst[R1 * k2] = v[k2];
     }
     __syncthreads();
+}
+
+// Inverse x-transform whose input lines arrive as half rows: line l holds, as float4 at element 2k,
+// (W_a[k], W_b[k]) for k < L/2, the x-spectra of the two real rows of a row pair.  Pass 1 rebuilds
+// Z[n] = W_a[n] + i W_b[n] with the Hermitian mirror Z[L-n] = conj(W_a[n]) + i conj(W_b[n]), and
+// the packed k = 0 entry (real DC in .x, real Nyquist in .y) as Z[0] and Z[L/2], on the fly.
+// The data area is overwritten with Z's transform in natural order.
+template <int L, int NL, int NF, int P, int AREA, int NT>
+__device__ __forceinline__ void ifft_halfrows_ct(float2* data, float2* xch, const float2* __restrict__ tw) {
+    constexpr int DIR = +1;
+    constexpr int R1 = Split<L>::B;
+    constexpr int R2 = L / R1;
+    static_assert(L <= P, "line pitch too small");
+    const int tid = threadIdx.x;
+#pragma unroll 1
+    for (int it = tid; it < NF * NL * R2; it += NT) {
+        const int t = it % R2, lf = it / R2;
+        const int off = (lf / NL) * AREA + (lf % NL) * P;
+        const float4* half = reinterpret_cast<const float4*>(data + off);
+        float2 v[R1];
+#pragma unroll
+        for (int m = 0; m < R1; m++) {
+            const int n = t + R2 * m;
+            if (n == 0 || n == L / 2) {
+                const float4 w = half[0];
+                v[m] = (n == 0) ? make_float2(w.x, w.z) : make_float2(w.y, w.w);
+            } else if (n < L / 2) {
+                const float4 w = half[n];
+                v[m] = make_float2(w.x - w.w, w.y + w.z);
+            } else {
+                const float4 w = half[L - n];
+                v[m] = make_float2(w.x + w.w, w.z - w.y);
+            }
+        }
+        Dft<R1, DIR>::run(v);
+        float2* dst = xch + off;
+#pragma unroll
+        for (int k1 = 0; k1 < R1; k1++) {
+            const float2 w = (k1 == 0) ? v[k1] : cmul(v[k1], twiddle<L, DIR>(tw, t * k1));
+            dst[xswz<R2>(k1, t)] = w;
+        }
+    }
+    __syncthreads();
+#pragma unroll 1
+    for (int it = tid; it < NF * NL * R1; it += NT) {
+        const int k1 = it % R1, lf = it / R1;
+        const int off = (lf / NL) * AREA + (lf % NL) * P;
+        float2 v[R2];
+        const float2* src = xch + off;
+#pragma unroll
+        for (int t = 0; t < R2; t++) v[t] = src[xswz<R2>(k1, t)];
+        Dft<R2, DIR>::run(v);
+        float2* dst = data + off + k1;
+#pragma unroll
+        for (int k2 = 0; k2 < R2; k2++) dst[R1 * k2] = v[k2];
+    }
+    __syncthreads();
+}
+
+// Cluster barriers.  cluster_sync_release orders this CTA's earlier memory operations (the
+// distributed-shared-memory writes of a transpose) before every CTA's later ones; cluster_sync_relaxed
+// is a pure execution barrier, used where a CTA only needs to know that the others have finished
+// reading a buffer, so it does not wait for earlier global stores to drain.
+__device__ __forceinline__ void cluster_sync_release() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void cluster_sync_relaxed() {
+    asm volatile("barrier.cluster.arrive.relaxed.aligned;\n\tbarrier.cluster.wait.aligned;" ::: "memory");
 }
 
 }  // namespace pat

@@ -41,7 +41,7 @@ struct Geom {
 
 struct DeviceTables {
     float2* tw[3];              // FFT twiddles exp(-2 pi i m / L) per axis length
-    float* kappaN;              // kappa(|k|) / N on the half spectrum [nz][ny][nxh]
+    float* kappaN;              // kappa(|k|) / N on the half spectrum [nz][nxh][ny]
     float2* dplus[3];           // i k exp(+i k dx/2) per axis (x: nxh entries)
     float2* dminus[3];          // i k exp(-i k dx/2)
     float* coef[CT_COUNT][3];   // per-axis coefficient tables
@@ -49,7 +49,7 @@ struct DeviceTables {
 
 struct Workspace {
     float* st[6];               // u_z,u_y,u_x,rho_z,rho_y,rho_x (forward) / v_i, q_i (adjoint)
-    float2* spec[3];            // half spectra [B][nz][ny][nxh]
+    float2* spec[3];            // half spectra [B][nz][nxh][ny] (one allocation)
     float* rec;                 // recorded / injected plane series [B][T][M] (sampled kinds)
     int32_t* idx;               // POINTS index list
     int32_t* perm;              // HADAMARD scramble

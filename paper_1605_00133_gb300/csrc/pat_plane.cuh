@@ -4,7 +4,8 @@
 //   ROW: complex row pairs j in [r*RC, (r+1)*RC), Z_j[x] = r[2j][x] + i r[2j+1][x] (x-FFT lines),
 //   COL: packed half-spectrum columns kx' in [r*CC, (r+1)*CC) over all ky (y-FFT lines),
 // for up to three fields at once.  The x-DC and x-Nyquist columns, both real after the x-FFT, share
-// the packed column kx' = 0 as D + i Nq.  The transpose between the row and column layouts goes
+// the packed column kx' = 0 as D + i Nq.  Half spectra are stored [z][kx][ky] (ky fastest), so a
+// CTA's columns are one contiguous run of CC * NY complex values per plane.  The transpose between the row and column layouts goes
 // through distributed shared memory (map_shared_rank) between two cluster barriers.  While one slab
 // is being transformed the other one is idle, so it doubles as the transform's exchange buffer.
 //
@@ -36,7 +37,9 @@ struct PS {
     static constexpr int RC = NY / 2 / CS;                       // row pairs per CTA
     static constexpr int CC = NX / 2 / CS;                       // packed columns per CTA
     static constexpr int NXH = NX / 2 + 1;
-    static constexpr int P = cmax(NX, NY) + 17;                  // line pitch (odd: no bank aliasing)
+    // line pitch: >= the longest line, and = 8 (mod 16) so that a half-warp spanning two lines
+    // touches 16 distinct 8-byte bank pairs
+    static constexpr int P = ((cmax(NX, NY) + 7) / 16) * 16 + 8;
     static constexpr int AREA = cmax(RC, CC) * P;                // one field's slab
     static constexpr int NT = kPlaneThreads;
     static constexpr size_t smem(int nf) { return (size_t)2 * nf * AREA * sizeof(float2); }
@@ -53,40 +56,47 @@ __device__ __forceinline__ void inv_planes(const PlaneArgs& a, float2* ROW, floa
     using S = PS<NX, NY>;
     constexpr int CC = S::CC, RC = S::RC, P = S::P, AREA = S::AREA, NT = S::NT;
     const int tid = threadIdx.x;
-#pragma unroll 1
-    for (int it = tid; it < NF * NY * CC; it += NT) {
-        const int c = it % CC, ky = (it / CC) % NY, f = it / (CC * NY);
-        const int kx = rank * CC + c;
-        const float2* s = sp + f * fs + ky * S::NXH;
-        float2 v = s[kx];
-        if (kx == 0) {
-            const float2 q = s[NX / 2];
-            v = make_float2(v.x - q.y, v.y + q.x);
+    // every load is issued before any is consumed (one L2 round trip, not one per element)
+    constexpr int NLD = (NF * NY * CC + NT - 1) / NT;
+    float2 v[NLD];
+#pragma unroll
+    for (int u = 0; u < NLD; u++) {
+        const int it = tid + u * NT;
+        v[u] = make_float2(0.f, 0.f);
+        if (NLD * NT == NF * NY * CC || it < NF * NY * CC) {
+            const int ky = it % NY, c = (it / NY) % CC, f = it / (CC * NY);
+            const int kx = rank * CC + c;
+            const float2* s = sp + f * fs;
+            v[u] = s[kx * NY + ky];
+            if (kx == 0) {
+                const float2 q = s[(NX / 2) * NY + ky];
+                v[u] = make_float2(v[u].x - q.y, v[u].y + q.x);
+            }
         }
-        COL[f * AREA + c * P + ky] = v;
+    }
+#pragma unroll
+    for (int u = 0; u < NLD; u++) {
+        const int it = tid + u * NT;
+        if (NLD * NT == NF * NY * CC || it < NF * NY * CC) {
+            const int ky = it % NY, c = (it / NY) % CC, f = it / (CC * NY);
+            COL[f * AREA + c * P + ky] = v[u];
+        }
     }
     __syncthreads();
     fft_lines_ct<NY, +1, CC, NF, P, AREA, NT>(COL, ROW, a.tw_y);
-    cl.sync();  // every CTA's ROW is free
+    cluster_sync_relaxed();  // every CTA has finished using its ROW as exchange space
     constexpr int NYH = NY / 2;
 #pragma unroll 1
     for (int it = tid; it < NF * CC * NYH; it += NT) {
-        const int c = it % CC, j = (it / CC) % NYH, f = it / (CC * NYH);
+        const int j = it % NYH, c = (it / NYH) % CC, f = it / (CC * NYH);
         const int kx = rank * CC + c;
-        const float2 wa = COL[f * AREA + c * P + 2 * j];
-        const float2 wb = COL[f * AREA + c * P + 2 * j + 1];
+        const float4 w = *reinterpret_cast<const float4*>(COL + f * AREA + c * P + 2 * j);  // rows 2j, 2j+1
         const int dst = j / RC, jl = j % RC;
-        float2* rr = cl.map_shared_rank(ROW, dst) + f * AREA + jl * P;
-        if (kx == 0) {
-            rr[0] = make_float2(wa.x, wb.x);
-            rr[NX / 2] = make_float2(wa.y, wb.y);
-        } else {
-            rr[kx] = make_float2(wa.x - wb.y, wa.y + wb.x);
-            rr[NX - kx] = make_float2(wa.x + wb.y, wb.x - wa.y);
-        }
+        float4* rr = reinterpret_cast<float4*>(cl.map_shared_rank(ROW, dst) + f * AREA + jl * P);
+        rr[kx] = w;  // half row: (W_a[kx], W_b[kx]); column 0 carries (DC, Nyquist) of both rows
     }
-    cl.sync();
-    fft_lines_ct<NX, +1, RC, NF, P, AREA, NT>(ROW, COL, a.tw_x);
+    cluster_sync_release();
+    ifft_halfrows_ct<NX, RC, NF, P, AREA, NT>(ROW, COL, a.tw_x);
 }
 
 // Forward (y,x) transform of NF ROW slabs into half-spectrum planes at sp + f*fs.
@@ -97,7 +107,7 @@ __device__ __forceinline__ void fwd_planes(const PlaneArgs& a, float2* ROW, floa
     constexpr int CC = S::CC, RC = S::RC, P = S::P, AREA = S::AREA, NT = S::NT;
     const int tid = threadIdx.x;
     fft_lines_ct<NX, -1, RC, NF, P, AREA, NT>(ROW, COL, a.tw_x);
-    cl.sync();  // every CTA's COL is free
+    cluster_sync_relaxed();  // every CTA has finished using its COL as exchange space
     constexpr int NXQ = NX / 2;
 #pragma unroll 1
     for (int it = tid; it < NF * RC * NXQ; it += NT) {
@@ -106,34 +116,32 @@ __device__ __forceinline__ void fwd_planes(const PlaneArgs& a, float2* ROW, floa
         const float2* row = ROW + f * AREA + jl * P;
         const float2 zk = row[k];
         const int dst = k / CC, c = k % CC;
-        float2* cr = cl.map_shared_rank(COL, dst) + f * AREA + c * P;
+        float4* cr = reinterpret_cast<float4*>(cl.map_shared_rank(COL, dst) + f * AREA + c * P + 2 * jg);
         if (k == 0) {
             const float2 zn = row[NXQ];
-            cr[2 * jg] = make_float2(zk.x, zn.x);
-            cr[2 * jg + 1] = make_float2(zk.y, zn.y);
+            *cr = make_float4(zk.x, zn.x, zk.y, zn.y);
         } else {
             const float2 zm = cconj(row[NX - k]);
-            const float2 d = csub(zk, zm);
-            cr[2 * jg] = cscale(cadd(zk, zm), 0.5f);
-            cr[2 * jg + 1] = make_float2(0.5f * d.y, -0.5f * d.x);
+            const float2 sm = cadd(zk, zm), d = csub(zk, zm);
+            *cr = make_float4(0.5f * sm.x, 0.5f * sm.y, 0.5f * d.y, -0.5f * d.x);
         }
     }
-    cl.sync();
+    cluster_sync_release();
     fft_lines_ct<NY, -1, CC, NF, P, AREA, NT>(COL, ROW, a.tw_y);
 #pragma unroll 1
     for (int it = tid; it < NF * NY * CC; it += NT) {
-        const int c = it % CC, ky = (it / CC) % NY, f = it / (CC * NY);
+        const int ky = it % NY, c = (it / NY) % CC, f = it / (CC * NY);
         const int kx = rank * CC + c;
         const float2* col = COL + f * AREA + c * P;
         const float2 v = col[ky];
-        float2* s = sp + f * fs + ky * S::NXH;
+        float2* s = sp + f * fs;
         if (kx == 0) {
             const float2 vm = cconj(col[(NY - ky) & (NY - 1)]);
             const float2 d = csub(v, vm);
-            s[0] = cscale(cadd(v, vm), 0.5f);
-            s[NX / 2] = make_float2(0.5f * d.y, -0.5f * d.x);
+            s[ky] = cscale(cadd(v, vm), 0.5f);
+            s[(NX / 2) * NY + ky] = make_float2(0.5f * d.y, -0.5f * d.x);
         } else {
-            s[kx] = v;
+            s[kx * NY + ky] = v;
         }
     }
     __syncthreads();
@@ -153,7 +161,7 @@ __device__ __forceinline__ PlaneIdx plane_idx(const PlaneArgs& a, cg::cluster_gr
     p.z = blockIdx.y;
     p.b = blockIdx.z;
     p.plane_off = ((size_t)p.b * g.nz + p.z) * (size_t)(NY * NX);
-    p.spec_off = (size_t)p.b * g.nspec + (size_t)p.z * (NY * PS<NX, NY>::NXH);
+    p.spec_off = (size_t)p.b * g.nspec + (size_t)p.z * (PS<NX, NY>::NXH * NY);
     p.rec_off = ((size_t)p.b * g.T + a.n_rec) * (size_t)(NY * NX);
     p.on_sensor = (p.z == g.sensor_z);
     p.fs = (size_t)g.B * g.nspec;
@@ -163,6 +171,7 @@ __device__ __forceinline__ PlaneIdx plane_idx(const PlaneArgs& a, cg::cluster_gr
 // Pointwise loops visit (row pair jl, x pair xp): rows y0 = 2 (rank RC + jl), y0 + 1 and columns
 // x0 = 2 xp, x0 + 1; ROW[f][jl][x] = (value at row y0, value at row y0 + 1).
 #define PAT_POINTWISE_BEGIN(S, I)                                                   \
+    _Pragma("unroll")                                                               \
     for (int it = threadIdx.x; it < S::RC * (NX / 2); it += S::NT) {                \
         const int xp = it % (NX / 2), jl = it / (NX / 2);                           \
         const int x0 = 2 * xp, y0 = 2 * (I.rank * S::RC + jl);                       \
@@ -171,7 +180,7 @@ __device__ __forceinline__ PlaneIdx plane_idx(const PlaneArgs& a, cg::cluster_gr
 #define PAT_POINTWISE_END }
 
 template <int NX, int NY>
-__global__ void __launch_bounds__(kPlaneThreads) plane_init_kernel(PlaneArgs a) {
+__global__ void __launch_bounds__(kPlaneThreads, 4) plane_init_kernel(PlaneArgs a) {
     using S = PS<NX, NY>;
     cg::cluster_group cl = cg::this_cluster();
     extern __shared__ float4 smem_raw[];
@@ -190,8 +199,7 @@ __global__ void __launch_bounds__(kPlaneThreads) plane_init_kernel(PlaneArgs a) 
         *reinterpret_cast<float2*>(a.rec + I.rec_off + (size_t)y0 * NX + x0) = pa;
         *reinterpret_cast<float2*>(a.rec + I.rec_off + (size_t)(y0 + 1) * NX + x0) = pb;
     }
-    ROW[rbase] = make_float2(pa.x, pb.x);
-    ROW[rbase + 1] = make_float2(pa.y, pb.y);
+    *reinterpret_cast<float4*>(ROW + rbase) = make_float4(pa.x, pb.x, pa.y, pb.y);
     PAT_POINTWISE_END
     __syncthreads();
     if (!(a.flags & PF_NO_FWD)) {
@@ -200,7 +208,7 @@ __global__ void __launch_bounds__(kPlaneThreads) plane_init_kernel(PlaneArgs a) 
 }
 
 template <int NX, int NY>
-__global__ void __launch_bounds__(kPlaneThreads) plane_vel_kernel(PlaneArgs a) {
+__global__ void __launch_bounds__(kPlaneThreads, 4) plane_vel_kernel(PlaneArgs a) {
     using S = PS<NX, NY>;
     cg::cluster_group cl = cg::this_cluster();
     extern __shared__ float4 smem_raw[];
@@ -215,7 +223,8 @@ __global__ void __launch_bounds__(kPlaneThreads) plane_vel_kernel(PlaneArgs a) {
 #pragma unroll
     for (int i = 0; i < 3; i++) {
         float2* rw = ROW + i * S::AREA + rbase;
-        const float2 z0 = rw[0], z1 = rw[1];  // (y0, y0+1) at x0 and at x0+1
+        const float4 zz = *reinterpret_cast<const float4*>(rw);  // (y0, y0+1) at x0 and at x0+1
+        const float2 z0 = make_float2(zz.x, zz.y), z1 = make_float2(zz.z, zz.w);
         const int qa = axis_pos(i, I.z, y0, x0), qb = axis_pos(i, I.z, y0, x0 + 1);
         const int qc = axis_pos(i, I.z, y0 + 1, x0), qd = axis_pos(i, I.z, y0 + 1, x0 + 1);
         const float* A1 = a.A1[i];
@@ -233,8 +242,8 @@ __global__ void __launch_bounds__(kPlaneThreads) plane_vel_kernel(PlaneArgs a) {
         }
         *reinterpret_cast<float2*>(a.st[i] + g0) = na;
         *reinterpret_cast<float2*>(a.st[i] + g1) = nb;
-        rw[0] = make_float2(__ldg(A3 + qa) * na.x, __ldg(A3 + qc) * nb.x);
-        rw[1] = make_float2(__ldg(A3 + qb) * na.y, __ldg(A3 + qd) * nb.y);
+        *reinterpret_cast<float4*>(rw) = make_float4(__ldg(A3 + qa) * na.x, __ldg(A3 + qc) * nb.x,
+                                                     __ldg(A3 + qb) * na.y, __ldg(A3 + qd) * nb.y);
     }
     PAT_POINTWISE_END
     __syncthreads();
@@ -242,7 +251,7 @@ __global__ void __launch_bounds__(kPlaneThreads) plane_vel_kernel(PlaneArgs a) {
 }
 
 template <int NX, int NY>
-__global__ void __launch_bounds__(kPlaneThreads) plane_rho_fwd_kernel(PlaneArgs a) {
+__global__ void __launch_bounds__(kPlaneThreads, 4) plane_rho_fwd_kernel(PlaneArgs a) {
     using S = PS<NX, NY>;
     cg::cluster_group cl = cg::this_cluster();
     extern __shared__ float4 smem_raw[];
@@ -257,7 +266,8 @@ __global__ void __launch_bounds__(kPlaneThreads) plane_rho_fwd_kernel(PlaneArgs 
 #pragma unroll
     for (int i = 0; i < 3; i++) {
         const float2* rw = ROW + i * S::AREA + rbase;
-        const float2 z0 = rw[0], z1 = rw[1];
+        const float4 zz = *reinterpret_cast<const float4*>(rw);
+        const float2 z0 = make_float2(zz.x, zz.y), z1 = make_float2(zz.z, zz.w);
         const int qa = axis_pos(i, I.z, y0, x0), qb = axis_pos(i, I.z, y0, x0 + 1);
         const int qc = axis_pos(i, I.z, y0 + 1, x0), qd = axis_pos(i, I.z, y0 + 1, x0 + 1);
         const float* A1 = a.A1[i];
@@ -281,8 +291,7 @@ __global__ void __launch_bounds__(kPlaneThreads) plane_rho_fwd_kernel(PlaneArgs 
         *reinterpret_cast<float2*>(a.rec + I.rec_off + (size_t)y0 * NX + x0) = pa;
         *reinterpret_cast<float2*>(a.rec + I.rec_off + (size_t)(y0 + 1) * NX + x0) = pb;
     }
-    ROW[rbase] = make_float2(pa.x, pb.x);
-    ROW[rbase + 1] = make_float2(pa.y, pb.y);
+    *reinterpret_cast<float4*>(ROW + rbase) = make_float4(pa.x, pb.x, pa.y, pb.y);
     PAT_POINTWISE_END
     __syncthreads();
     if (!(a.flags & PF_NO_FWD)) {
@@ -291,7 +300,7 @@ __global__ void __launch_bounds__(kPlaneThreads) plane_rho_fwd_kernel(PlaneArgs 
 }
 
 template <int NX, int NY>
-__global__ void __launch_bounds__(kPlaneThreads) plane_rho_adj_kernel(PlaneArgs a) {
+__global__ void __launch_bounds__(kPlaneThreads, 4) plane_rho_adj_kernel(PlaneArgs a) {
     using S = PS<NX, NY>;
     cg::cluster_group cl = cg::this_cluster();
     extern __shared__ float4 smem_raw[];
@@ -307,7 +316,8 @@ __global__ void __launch_bounds__(kPlaneThreads) plane_rho_adj_kernel(PlaneArgs 
     PAT_POINTWISE_BEGIN(S, I)
     float2 la = make_float2(0.f, 0.f), lb = make_float2(0.f, 0.f);  // rows y0, y0+1 at x0, x0+1
     if (have_lambda) {
-        const float2 z0 = ROW[rbase], z1 = ROW[rbase + 1];
+        const float4 zz = *reinterpret_cast<const float4*>(ROW + rbase);
+        const float2 z0 = make_float2(zz.x, zz.y), z1 = make_float2(zz.z, zz.w);
         la = make_float2(a.s0 * z0.x, a.s0 * z1.x);
         lb = make_float2(a.s0 * z0.y, a.s0 * z1.y);
     }
@@ -351,8 +361,8 @@ __global__ void __launch_bounds__(kPlaneThreads) plane_rho_adj_kernel(PlaneArgs 
             *reinterpret_cast<float2*>(a.st[i] + g0) = na;
             *reinterpret_cast<float2*>(a.st[i] + g1) = nb;
             float2* rw = ROW + i * S::AREA + rbase;
-            rw[0] = make_float2(__ldg(a.A3[i] + qa) * na.x, __ldg(a.A3[i] + qc) * nb.x);
-            rw[1] = make_float2(__ldg(a.A3[i] + qb) * na.y, __ldg(a.A3[i] + qd) * nb.y);
+            *reinterpret_cast<float4*>(rw) = make_float4(__ldg(a.A3[i] + qa) * na.x, __ldg(a.A3[i] + qc) * nb.x,
+                                                         __ldg(a.A3[i] + qb) * na.y, __ldg(a.A3[i] + qd) * nb.y);
         }
     }
     PAT_POINTWISE_END

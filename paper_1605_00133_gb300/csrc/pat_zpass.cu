@@ -1,7 +1,7 @@
 // pat_zpass.cu - z-pass kernels: z-FFT of the (y,x)-transformed fields, multiply by the staggered
 // k-space derivative i k_i kappa(|k|) exp(+/- i k_i dx / 2) / N, inverse z-FFT, all in one pass.
 //
-// A CTA owns TC consecutive half-spectrum columns (ky, kx) over all kz.  Each column's length-NZ
+// A CTA owns TC consecutive half-spectrum columns (kx, ky) over all kz.  Each column's length-NZ
 // transform is the two-pass split of pat_fft.cuh: pass 1 reads the column straight from global
 // memory into registers, the exchange goes through shared memory laid out [row][column] with the
 // column index fastest (consecutive threads touch consecutive words: no bank conflicts), pass 2
@@ -37,13 +37,13 @@ struct ZCtx {
         const int tid = threadIdx.x;
         cl = tid % S::TC;
         r = tid / S::TC;
-        const int ncols = a.g.ny * a.g.nxh;
+        const int ncols = a.g.ny * a.g.nxh;  // half-spectrum columns, stored (kx, ky) with ky fastest
         col = blockIdx.x * S::TC + cl;
         vcol = col < ncols;
         zst = (size_t)ncols;
         boff = (size_t)blockIdx.y * a.g.nspec;
-        ky = vcol ? col / a.g.nxh : 0;
-        kx = vcol ? col - ky * a.g.nxh : 0;
+        kx = vcol ? col / a.g.ny : 0;
+        ky = vcol ? col - kx * a.g.ny : 0;
     }
     // forward pass 1 of one column (role t = r < B) into buffer f
     __device__ __forceinline__ void f1(const float2* __restrict__ in, int f) {

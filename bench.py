@@ -29,6 +29,9 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 METRIC = "A+A^T pairs/s (64x128x128, 400 steps)"
+
+# (kernel source hash, workload, batch) -> DRAM bytes (read + write) of one time step, from ncu
+STEP_TRAFFIC = {("0993db717cb8", "c2", 1): 72.16e6}
 UNIT = "pairs/s"
 
 
@@ -264,15 +267,9 @@ def main():
     step_s = (ms / 1e3) / (args.steps * steps_per_pair)
     bytes_per_step = 48.0 * g.n * B
     achieved = bytes_per_step / step_s / 1e9
-    traffic = None
-    tpath = os.path.join(ROOT, "profiles", "traffic_per_step.json")
-    if os.path.exists(tpath):
-        try:
-            tt = _json.load(open(tpath))
-            if tt.get("workload") == w.name and tt.get("batch") == B and tt.get("source_hash") == _source_hash():
-                traffic = tt["dram_bytes_per_step"]
-        except Exception:
-            traffic = None
+    # DRAM bytes of one forward time step from the committed ncu capture, valid only for the kernel
+    # sources it was taken on (profiles/pat_step_kernels_c2.md)
+    traffic = STEP_TRAFFIC.get((_source_hash(), w.name, B))
     roofline = {"bound": "hbm", "kernel": "time step (zpass_grad3 + plane_vel + zpass_each3 + plane_rho_fwd, "
                                           "and the adjoint's four)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -309,7 +306,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        Ts = 16
+        Ts = 100
         v, t, threads = oracle_pairs_per_s(w, Ts)
         cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": (f"one oracle A + A^T on the full {g.nz}x{g.ny}x{g.nx} grid with T = {Ts} "

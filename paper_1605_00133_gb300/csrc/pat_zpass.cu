@@ -47,19 +47,41 @@ struct ZCtx {
     }
     // forward pass 1 of one column (role t = r < B) into buffer f
     __device__ __forceinline__ void f1(const float2* __restrict__ in, int f) {
-        constexpr int A = S::A, B = S::B, TC = S::TC;
+        constexpr int A = S::A, B = S::B;
         if (r < B && vcol) {
-            const int t = r;
             float2 v[A];
+            load(in, v);
+            f1_from(v, f);
+        }
+    }
+    // the column's values x[t + B m], m < A, of role t = r
+    __device__ __forceinline__ void load(const float2* __restrict__ in, float2* v) const {
+        constexpr int A = S::A, B = S::B;
 #pragma unroll
-            for (int m = 0; m < A; m++) v[m] = in[boff + (size_t)(t + B * m) * zst + col];
-            Dft<A, -1>::run(v);
-            float2* dst = buf + f * S::BUF + t * TC + cl;
+        for (int m = 0; m < A; m++) v[m] = in[boff + (size_t)(r + B * m) * zst + col];
+    }
+    __device__ __forceinline__ void f1_from(float2* v, int f) {
+        constexpr int A = S::A, B = S::B, TC = S::TC;
+        const int t = r;
+        Dft<A, -1>::run(v);
+        float2* dst = buf + f * S::BUF + t * TC + cl;
 #pragma unroll
-            for (int k1 = 0; k1 < A; k1++) {
-                const float2 w = (k1 == 0) ? v[k1] : cmul(v[k1], twiddle<NZ, -1>(a.tw_z, t * k1));
-                dst[k1 * B * TC] = w;
-            }
+        for (int k1 = 0; k1 < A; k1++) {
+            const float2 w = (k1 == 0) ? v[k1] : cmul(v[k1], twiddle<NZ, -1>(a.tw_z, t * k1));
+            dst[k1 * B * TC] = w;
+        }
+    }
+    // pass 1 of all three inputs, every global load issued before the first transform
+    __device__ __forceinline__ void f1_three() {
+        constexpr int A = S::A, B = S::B;
+        if (r < B && vcol) {
+            float2 v0[A], v1[A], v2[A];
+            load(a.spec[0], v0);
+            load(a.spec[1], v1);
+            load(a.spec[2], v2);
+            f1_from(v0, 0);
+            f1_from(v1, 1);
+            f1_from(v2, 2);
         }
     }
     // forward pass 2 (role k1 = r < A): v[k2] = X[k1 + A k2]
@@ -136,8 +158,7 @@ __global__ void __launch_bounds__(kZThreads) zpass_each3_kernel(ZArgs a) {
     constexpr int A = S::A, B = S::B;
     extern __shared__ float4 smem_raw[];
     ZCtx<NZ> c(a, reinterpret_cast<float2*>(smem_raw));
-#pragma unroll 1
-    for (int o = 0; o < 3; o++) c.f1(a.spec[o], o);
+    c.f1_three();
     __syncthreads();
     float2 v[3][B];
     if (c.vcol) {
@@ -164,8 +185,7 @@ __global__ void __launch_bounds__(kZThreads) zpass_sum3_kernel(ZArgs a) {
     constexpr int A = S::A, B = S::B;
     extern __shared__ float4 smem_raw[];
     ZCtx<NZ> c(a, reinterpret_cast<float2*>(smem_raw));
-#pragma unroll 1
-    for (int o = 0; o < 3; o++) c.f1(a.spec[o], o);
+    c.f1_three();
     __syncthreads();
     float2 acc[B];
 #pragma unroll

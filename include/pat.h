@@ -134,6 +134,52 @@ pat_status pat_sample(pat_grid* grid, const float* pbar_dev, float* f_dev, int32
 pat_status pat_sample_adjoint(pat_grid* grid, const float* f_dev, float* pbar_dev, int32_t nt,
                               void* cuda_stream);
 
+/* Positivity-constrained TV denoising, the proximal operator of the TV+ functional (Sec. 4.5
+ * Eq. TV+, App. A, App. B Eq. TV+Denoise):  out = argmin_{q >= 0} 1/2 ||q - in||^2 + alpha TV(q),
+ * TV(q) = sum over voxels of |forward-difference gradient|_2, Neumann boundary (bc = 0; other
+ * values return PAT_ERR_UNSUPPORTED).  Solved by `iters` steps of the accelerated primal-dual
+ * hybrid gradient method (tau_0 = sigma_0 = 1/sqrt(12), theta = 1/sqrt(1 + 2 tau)), started at
+ * q = max(0, in).  in_dev / out_dev: float[B][Nz][Ny][Nx]; they may alias.  The first call on a
+ * grid allocates its prox workspace (4 image-sized FP32 buffers). */
+pat_status pat_tv_prox(pat_grid* grid, const float* in_dev, float* out_dev, double alpha, int32_t iters,
+                       int32_t bc, void* cuda_stream);
+
+/* Parameters of pat_bregman_solve (App. B: eta = step_scale / L with step_scale 1.8, up to 5
+ * backtracking halvings after a restart, stop when min E has not decreased 5 times in a row). */
+typedef struct {
+    double lambda;          /* TV weight (>= 0) */
+    int32_t outer;          /* Bregman iterations (>= 1; 1 = plain TV+) */
+    int32_t inner;          /* FISTA iterations per Bregman step (>= 1; the paper uses 50) */
+    int32_t prox_iters;     /* primal-dual iterations per TV prox (>= 1) */
+    double L;               /* Lipschitz constant of A^T C^T C A; <= 0: estimate by power iteration */
+    int32_t power_iters;    /* power iterations when L <= 0 (>= 1) */
+    uint64_t seed;          /* seed of the power-iteration start vector */
+    double step_scale;      /* eta = step_scale / L (> 0) */
+    int32_t max_backtrack;  /* step halvings after a restart (>= 0) */
+    int32_t stall;          /* early stop after this many steps without a new minimum of E (>= 1) */
+} pat_solve_params;
+
+typedef struct {
+    double L;               /* the Lipschitz constant used */
+    int32_t inner_total;    /* FISTA iterations done over all Bregman steps */
+    int32_t restarts;       /* momentum restarts */
+    double energy;          /* final E = 1/2 ||C A p - (f + b)||^2 + lambda TV(p) of the last step */
+    int32_t n_residual;     /* entries written to residual (<= 64) */
+    double residual[64];    /* ||C A p^k - f|| after Bregman step k (FP64) */
+} pat_solve_report;
+
+/* TV+ / TV+Br reconstruction (Sec. 4.5-4.6, Eqs. VarReg, TV+, BregIterA/B; App. B): Bregman
+ * iterations p^{k+1} = argmin_{p >= 0} 1/2 ||C A p - (f + b^k)||^2 + lambda TV(p),
+ * b^{k+1} = b^k + (f - C A p^{k+1}), b^0 = 0, each solved by FISTA with restart and backtracking
+ * (one pat_forward and one pat_adjoint per iteration, plus extra ones on a restart), warm-started
+ * from the previous p.  f_dev: float[1][T][m]; warm_dev: float[1][Nz][Ny][Nx] start or NULL (zero);
+ * p_out_dev: float[1][Nz][Ny][Nx].  Batch must be 1.  The Bregman variable, the objective and all
+ * norms are accumulated in FP64.  The call synchronises the stream after each FP64 reduction (the
+ * host takes the restart / stopping decisions).  The first call allocates the solver workspace.
+ * report may be NULL. */
+pat_status pat_bregman_solve(pat_grid* grid, const float* f_dev, const float* warm_dev, float* p_out_dev,
+                             const pat_solve_params* params, pat_solve_report* report, void* cuda_stream);
+
 /* Kernel timing for benchmarks: while enabled, every kernel launch of pat_forward / pat_adjoint is
  * bracketed by CUDA events recorded on the call's stream.  pat_profile_enable(grid, 1) starts (and
  * clears) the record; pat_profile_read waits for the recorded events, then reports per kernel class

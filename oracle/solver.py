@@ -108,9 +108,9 @@ def tv_prox(p, alpha, iters=200, nonneg=True, return_dual=False):
 
 # --------------------------------------------------------------------------------- solver (App. B, Sec. 4.6)
 
-def power_iteration(g, s, iters=20, seed=0):
-    """L ~ ||A^T C^T C A||_2 by power iteration from a seeded Gaussian start."""
-    x = np.random.default_rng(seed).standard_normal(g.shape)
+def power_iteration(g, s, iters=20, seed=0, x0=None):
+    """L ~ ||A^T C^T C A||_2 by power iteration from x0 (default: a seeded Gaussian start)."""
+    x = np.random.default_rng(seed).standard_normal(g.shape) if x0 is None else np.array(x0, np.float64)
     x /= np.linalg.norm(x)
     lam = 0.0
     for _ in range(iters):

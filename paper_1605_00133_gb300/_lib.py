@@ -17,7 +17,8 @@ STATUS_NAMES = {0: "PAT_OK", 1: "PAT_ERR_INVALID_ARG", 2: "PAT_ERR_CUDA", 3: "PA
 # every symbol include/pat.h declares
 EXPORTS = ["pat_create_grid", "pat_destroy_grid", "pat_grid_info", "pat_workspace_bytes",
            "pat_forward", "pat_adjoint", "pat_sample", "pat_sample_adjoint", "pat_profile_enable",
-           "pat_profile_read", "pat_last_error", "pat_version", "pat_forward_noalloc"]
+           "pat_profile_read", "pat_last_error", "pat_version", "pat_forward_noalloc", "pat_tv_prox",
+           "pat_bregman_solve"]
 
 
 class PatError(RuntimeError):
@@ -38,6 +39,19 @@ class SamplingDesc(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int32), ("m", ctypes.c_int32),
                 ("indices", ctypes.POINTER(ctypes.c_int32)), ("perm", ctypes.POINTER(ctypes.c_int32)),
                 ("rows", ctypes.POINTER(ctypes.c_int32))]
+
+
+class SolveParams(ctypes.Structure):
+    _fields_ = [("lambda_", ctypes.c_double), ("outer", ctypes.c_int32), ("inner", ctypes.c_int32),
+                ("prox_iters", ctypes.c_int32), ("L", ctypes.c_double), ("power_iters", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("step_scale", ctypes.c_double),
+                ("max_backtrack", ctypes.c_int32), ("stall", ctypes.c_int32)]
+
+
+class SolveReport(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_double), ("inner_total", ctypes.c_int32), ("restarts", ctypes.c_int32),
+                ("energy", ctypes.c_double), ("n_residual", ctypes.c_int32),
+                ("residual", ctypes.c_double * 64)]
 
 
 _lock = threading.Lock()
@@ -73,6 +87,11 @@ def load() -> ctypes.CDLL:
             fn = getattr(L, name)
             fn.argtypes = [vp, vp, vp, ctypes.c_int32, vp]
             fn.restype = ctypes.c_int
+        L.pat_tv_prox.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_int32, ctypes.c_int32, vp]
+        L.pat_tv_prox.restype = ctypes.c_int
+        L.pat_bregman_solve.argtypes = [vp, vp, vp, vp, ctypes.POINTER(SolveParams),
+                                        ctypes.POINTER(SolveReport), vp]
+        L.pat_bregman_solve.restype = ctypes.c_int
         L.pat_profile_enable.argtypes = [vp, ctypes.c_int32]
         L.pat_profile_enable.restype = ctypes.c_int
         L.pat_profile_read.argtypes = [vp, ctypes.c_int32, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),

@@ -40,19 +40,6 @@ bool pow2_in(int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v - 1))
 
 }  // namespace
 
-struct pat_grid {
-    pat_grid_desc d;
-    int kind;
-    int m;
-    int device;
-    Geom g;
-    Scalars s;
-    DeviceTables t;
-    Workspace w;
-    std::vector<void*> allocs;
-    int64_t bytes;
-    Profiler prof;
-};
 
 namespace {
 
@@ -84,6 +71,7 @@ void free_grid(pat_grid* G) {
     if (!G) return;
     for (void* p : G->allocs) cudaFree(p);
     for (cudaEvent_t e : G->prof.pool) cudaEventDestroy(e);
+    if (G->sw.host) cudaFreeHost(G->sw.host);
     delete G;
 }
 
@@ -240,6 +228,13 @@ pat_status check_device(const pat_grid* G) {
 }
 
 }  // namespace
+
+namespace pat {
+pat_status set_error(pat_status s, const char* msg) { return fail(s, msg); }
+pat_status set_cuda_error(cudaError_t e, const char* where) { return cuda_fail(e, where); }
+pat_status grid_alloc(pat_grid* G, void** p, size_t bytes, const char* what) { return dalloc(G, p, bytes, what); }
+pat_status check_grid_device(const pat_grid* G) { return check_device(G); }
+}  // namespace pat
 
 extern "C" {
 

@@ -7,6 +7,8 @@
 
 #include "../../include/pat.h"
 
+struct pat_grid;
+
 namespace pat {
 
 enum Axis { AZ = 0, AY = 1, AX = 2 };
@@ -96,4 +98,39 @@ cudaError_t run_sample(const Geom& g, const Workspace& w, int kind, int m, const
 cudaError_t run_sample_adjoint(const Geom& g, const Workspace& w, int kind, int m, const float* f,
                                float* pbar, int nt, cudaStream_t st);
 
+// Solver workspace, allocated by the first pat_tv_prox / pat_bregman_solve call on a grid.
+struct SolverWs {
+    size_t n_img = 0, n_dat = 0;  // per-call sizes the buffers were made for
+    float *x = nullptr, *xp = nullptr, *y = nullptr, *z = nullptr, *grad = nullptr;  // image, B*N
+    float *qbar = nullptr, *xi = nullptr;                                          // prox: N, 3N
+    float *ax = nullptr, *axp = nullptr, *ay = nullptr, *r = nullptr;              // data, T*m
+    double *gdat = nullptr, *bdat = nullptr;                                        // data, FP64
+    double *partial = nullptr, *result = nullptr;                                   // reductions
+    double* host = nullptr;                                                         // pinned
+};
+
 }  // namespace pat
+
+namespace pat {
+// Error reporting and workspace allocation shared by the C-ABI translation units (pat_api.cu).
+pat_status set_error(pat_status s, const char* msg);
+pat_status set_cuda_error(cudaError_t e, const char* where);
+pat_status grid_alloc(pat_grid* G, void** p, size_t bytes, const char* what);
+pat_status check_grid_device(const pat_grid* G);
+}  // namespace pat
+
+// The grid handle (opaque to C callers).
+struct pat_grid {
+    pat_grid_desc d;
+    int kind;
+    int m;
+    int device;
+    pat::Geom g;
+    pat::Scalars s;
+    pat::DeviceTables t;
+    pat::Workspace w;
+    std::vector<void*> allocs;
+    int64_t bytes;
+    pat::Profiler prof;
+    pat::SolverWs sw;
+};

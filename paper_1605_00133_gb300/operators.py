@@ -113,6 +113,38 @@ class PatOperator:
                                                   _stream_ptr(f.device)))
         return pbar
 
+    # ------------------------------------------------------------------ variational reconstruction
+    def tv_prox(self, p: torch.Tensor, alpha: float, iters: int = 200, out: torch.Tensor = None):
+        """argmin_{q >= 0} 1/2 ||q - p||^2 + alpha TV(q) (pat_tv_prox, Neumann boundary)."""
+        self._check_tensor(p, self.image_shape, "p")
+        if out is None:
+            out = torch.empty_like(p)
+        self._check_tensor(out, self.image_shape, "out")
+        _lib.check(_lib.load().pat_tv_prox(self._h, p.data_ptr(), out.data_ptr(), float(alpha), int(iters),
+                                           0, _stream_ptr(p.device)))
+        return out
+
+    def bregman_solve(self, f: torch.Tensor, lam: float, outer: int = 5, inner: int = 50,
+                      prox_iters: int = 100, L: float = 0.0, power_iters: int = 20, seed: int = 0,
+                      step_scale: float = 1.8, max_backtrack: int = 5, stall: int = 5,
+                      warm: torch.Tensor = None, out: torch.Tensor = None):
+        """TV+ (outer = 1) or TV+Br reconstruction from data f (pat_bregman_solve).
+        Returns (p, report dict)."""
+        self._check_tensor(f, self.data_shape, "f")
+        if warm is not None:
+            self._check_tensor(warm, self.image_shape, "warm")
+        if out is None:
+            out = torch.empty(self.image_shape, device=f.device, dtype=torch.float32)
+        P = _lib.SolveParams(float(lam), int(outer), int(inner), int(prox_iters), float(L), int(power_iters),
+                             int(seed), float(step_scale), int(max_backtrack), int(stall))
+        R = _lib.SolveReport()
+        _lib.check(_lib.load().pat_bregman_solve(self._h, f.data_ptr(), warm.data_ptr() if warm is not None else None,
+                                                 out.data_ptr(), ctypes.byref(P), ctypes.byref(R),
+                                                 _stream_ptr(f.device)))
+        rep = {"L": R.L, "inner_total": R.inner_total, "restarts": R.restarts, "energy": R.energy,
+               "residuals": [R.residual[i] for i in range(R.n_residual)]}
+        return out, rep
+
     # ------------------------------------------------------------------ kernel timing
     def profile(self, enable: bool = True) -> None:
         """Bracket every kernel launch with CUDA events (see pat_profile_enable)."""

@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--solve", action="store_true",
+                    help="also time one TV-Bregman reconstruction of the workload (reported, not the metric)")
     return ap.parse_args()
 
 
@@ -304,6 +306,25 @@ def main():
         e2e = {"value": pairs / (ms_e2e / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": int(p0_h.numel() * 4), "d2h_bytes_per_step": int(p_h.numel() * 4)}
 
+    solve = None
+    if args.solve and B == 1:
+        # one TV+Br reconstruction: outer x inner FISTA steps (one A + A^T pair each, plus restarts)
+        from paper_1605_00133_gb300.presets import workload as _wl
+        wl = _wl(args.workload)
+        fnoisy = f + 0.01 * float(f.abs().max()) * torch.randn(f.shape, device=dev,
+                                                                generator=torch.Generator(device=dev).manual_seed(5))
+        lam = 2e-4
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        prec, rep = op.bregman_solve(fnoisy, lam, outer=wl.bregman_outer, inner=wl.inner, prox_iters=50,
+                                     power_iters=20)
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - t0
+        solve = {"seconds": secs, "outer": wl.bregman_outer, "inner": wl.inner, "prox_iters": 50,
+                 "lambda": lam, "power_iters": 20, "fista_iterations": rep["inner_total"],
+                 "restarts": rep["restarts"], "residuals": rep["residuals"],
+                 "rel_err_vs_phantom": float((prec - p0).norm() / p0.norm())}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         Ts = 100
@@ -319,6 +340,8 @@ def main():
                 "config": workload_config(w, B), "clocks": clk, "e2e": e2e,
                 "gpu_launches": int(round(launches_per_step * args.steps)),
                 "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu}
+        if solve is not None:
+            line["solve"] = solve
         print(json.dumps(line), flush=True)
     op.close()
     if dist:

@@ -197,6 +197,15 @@ __device__ __forceinline__ void ifft_halfrows_ct(float2* data, float2* xch, cons
     __syncthreads();
 }
 
+// Programmatic dependent launch.  Kernels of the time loop are launched with programmatic stream
+// serialisation, so a kernel's CTAs can become resident while its predecessor is still running.
+// pdl_wait() blocks until the predecessor grid has completed and its writes are visible; every
+// such kernel calls it before its first global-memory access.  pdl_trigger() lets the successor be
+// scheduled as soon as every CTA of this grid has issued it (the successor still waits for this
+// grid's completion before touching its outputs).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Cluster barriers.  cluster_sync_release orders this CTA's earlier memory operations (the
 // distributed-shared-memory writes of a transpose) before every CTA's later ones; cluster_sync_relaxed
 // is a pure execution barrier, used where a CTA only needs to know that the others have finished

@@ -8,7 +8,7 @@
 namespace pat {
 
 static constexpr int kPlaneThreads = 256;
-static constexpr int kZThreads = 256;
+static constexpr int kZCols = 32;  // half-spectrum columns per z-pass CTA
 
 enum PlaneFlag { PF_NO_FWD = 1, PF_NO_OLD = 2, PF_HAVE_LAMBDA = 4, PF_FINAL = 8 };
 
@@ -59,7 +59,8 @@ typedef void (*ZKernel)(ZArgs);
 struct ZKernels {
     ZKernel grad3 = nullptr, each3 = nullptr, sum3 = nullptr;
     size_t smem = 0;
-    int tc = 0;
+    int tc = 0;  // columns per CTA
+    int nt = 0;  // threads per CTA
 };
 
 ZKernels z_kernels_for(int nz);

@@ -187,6 +187,8 @@ __global__ void __launch_bounds__(kPlaneThreads, 4) plane_init_kernel(PlaneArgs 
     float2* ROW = reinterpret_cast<float2*>(smem_raw);
     float2* COL = ROW + S::AREA;
     const PlaneIdx I = plane_idx<NX, NY>(a, cl);
+    pdl_wait();
+    pdl_trigger();
     PAT_POINTWISE_BEGIN(S, I)
     const float2 pa = *reinterpret_cast<const float2*>(a.in_real + g0);  // row y0, x0..x0+1
     const float2 pb = *reinterpret_cast<const float2*>(a.in_real + g1);  // row y0+1
@@ -215,6 +217,8 @@ __global__ void __launch_bounds__(kPlaneThreads, 4) plane_vel_kernel(PlaneArgs a
     float2* ROW = reinterpret_cast<float2*>(smem_raw);
     float2* COL = ROW + 3 * S::AREA;
     const PlaneIdx I = plane_idx<NX, NY>(a, cl);
+    pdl_wait();
+    pdl_trigger();
     {
         inv_planes<NX, NY, 3>(a, ROW, COL, a.spec[0] + I.spec_off, I.fs, I.rank, cl);
     }
@@ -258,6 +262,8 @@ __global__ void __launch_bounds__(kPlaneThreads, 4) plane_rho_fwd_kernel(PlaneAr
     float2* ROW = reinterpret_cast<float2*>(smem_raw);
     float2* COL = ROW + 3 * S::AREA;
     const PlaneIdx I = plane_idx<NX, NY>(a, cl);
+    pdl_wait();
+    pdl_trigger();
     {
         inv_planes<NX, NY, 3>(a, ROW, COL, a.spec[0] + I.spec_off, I.fs, I.rank, cl);
     }
@@ -307,6 +313,8 @@ __global__ void __launch_bounds__(kPlaneThreads, 4) plane_rho_adj_kernel(PlaneAr
     float2* ROW = reinterpret_cast<float2*>(smem_raw);
     float2* COL = ROW + 3 * S::AREA;
     const PlaneIdx I = plane_idx<NX, NY>(a, cl);
+    pdl_wait();
+    pdl_trigger();
     const bool have_lambda = (a.flags & PF_HAVE_LAMBDA) != 0;
     if (have_lambda) {
         inv_planes<NX, NY, 1>(a, ROW, COL, a.spec[0] + I.spec_off, I.fs, I.rank, cl);

@@ -72,6 +72,8 @@ static cudaError_t timed(Profiler* prof, int cls, cudaStream_t st, F&& launch) {
     return cudaSuccess;
 }
 
+// Time-loop kernels are launched with programmatic stream serialisation (they call pdl_wait()
+// before touching memory), so each one is scheduled while its predecessor drains.
 static cudaError_t launch_plane(PlaneKernel k, size_t smem, int cs, const PlaneArgs& a, cudaStream_t st) {
     const Geom& g = a.g;
     cudaLaunchConfig_t cfg = {};
@@ -79,21 +81,31 @@ static cudaError_t launch_plane(PlaneKernel k, size_t smem, int cs, const PlaneA
     cfg.blockDim = dim3(kPlaneThreads, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = cs;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = 2;
     return cudaLaunchKernelEx(&cfg, k, a);
 }
 
 static cudaError_t launch_z(ZKernel k, const ZKernels& zk, const ZArgs& a, cudaStream_t st) {
     const int ncols = a.g.ny * a.g.nxh;
-    dim3 grid((ncols + zk.tc - 1) / zk.tc, a.g.B, 1);
-    k<<<grid, kZThreads, zk.smem, st>>>(a);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((ncols + zk.tc - 1) / zk.tc, a.g.B, 1);
+    cfg.blockDim = dim3(zk.nt, 1, 1);
+    cfg.dynamicSmemBytes = zk.smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k, a);
 }
 
 static PlaneArgs plane_base(const Geom& g, const DeviceTables& t, const Workspace& w) {

@@ -19,7 +19,8 @@ template <int NZ>
 struct ZS {
     static constexpr int A = Split<NZ>::A;  // forward R1 = inverse R2
     static constexpr int B = Split<NZ>::B;  // forward R2 = inverse R1
-    static constexpr int TC = kZThreads / A;
+    static constexpr int TC = kZCols;
+    static constexpr int NT = A * TC;       // threads per CTA
     static constexpr int BUF = NZ * TC;     // one field's exchange buffer (float2)
     static constexpr size_t smem = 3 * (size_t)BUF * sizeof(float2);
 };
@@ -93,9 +94,14 @@ struct ZCtx {
         Dft<B, -1>::run(v);
         (void)A;
     }
-    // k-space factor of axis o at kz
-    __device__ __forceinline__ float2 mult(int o, int kz) const {
-        const float kap = __ldg(a.kappaN + (size_t)kz * zst + col);
+    // kappa(|k|)/N at this thread's kz = r + A k2 (pass-2 role), loaded with the first pass's data
+    __device__ __forceinline__ void load_kappa(float* kap) const {
+        constexpr int A = S::A, B = S::B;
+#pragma unroll
+        for (int k2 = 0; k2 < B; k2++) kap[k2] = vcol ? __ldg(a.kappaN + (size_t)(r + A * k2) * zst + col) : 0.f;
+    }
+    // k-space factor of axis o at kz, given kappa/N there
+    __device__ __forceinline__ float2 mult(int o, int kz, float kap) const {
         const int ki = (o == 0) ? kz : (o == 1 ? ky : kx);
         return cscale(__ldg(a.dt[o] + ki), kap);
     }
@@ -128,11 +134,15 @@ struct ZCtx {
 };
 
 template <int NZ>
-__global__ void __launch_bounds__(kZThreads) zpass_grad3_kernel(ZArgs a) {
+__global__ void __launch_bounds__(ZS<NZ>::NT) zpass_grad3_kernel(ZArgs a) {
     using S = ZS<NZ>;
     constexpr int A = S::A, B = S::B;
     extern __shared__ float4 smem_raw[];
     ZCtx<NZ> c(a, reinterpret_cast<float2*>(smem_raw));
+    pdl_wait();
+    pdl_trigger();
+    float kap[B];
+    c.load_kappa(kap);
     c.f1(a.spec[0], 0);
     __syncthreads();
     float2 v[B];
@@ -143,7 +153,7 @@ __global__ void __launch_bounds__(kZThreads) zpass_grad3_kernel(ZArgs a) {
         for (int o = 0; o < 3; o++) {
             float2 w[B];
 #pragma unroll
-            for (int k2 = 0; k2 < B; k2++) w[k2] = cmul(v[k2], c.mult(o, c.r + A * k2));
+            for (int k2 = 0; k2 < B; k2++) w[k2] = cmul(v[k2], c.mult(o, c.r + A * k2, kap[k2]));
             c.i1(w, o);
         }
     }
@@ -153,11 +163,15 @@ __global__ void __launch_bounds__(kZThreads) zpass_grad3_kernel(ZArgs a) {
 }
 
 template <int NZ>
-__global__ void __launch_bounds__(kZThreads) zpass_each3_kernel(ZArgs a) {
+__global__ void __launch_bounds__(ZS<NZ>::NT) zpass_each3_kernel(ZArgs a) {
     using S = ZS<NZ>;
     constexpr int A = S::A, B = S::B;
     extern __shared__ float4 smem_raw[];
     ZCtx<NZ> c(a, reinterpret_cast<float2*>(smem_raw));
+    pdl_wait();
+    pdl_trigger();
+    float kap[B];
+    c.load_kappa(kap);
     c.f1_three();
     __syncthreads();
     float2 v[3][B];
@@ -170,7 +184,7 @@ __global__ void __launch_bounds__(kZThreads) zpass_each3_kernel(ZArgs a) {
 #pragma unroll
         for (int o = 0; o < 3; o++) {
 #pragma unroll
-            for (int k2 = 0; k2 < B; k2++) v[o][k2] = cmul(v[o][k2], c.mult(o, c.r + A * k2));
+            for (int k2 = 0; k2 < B; k2++) v[o][k2] = cmul(v[o][k2], c.mult(o, c.r + A * k2, kap[k2]));
             c.i1(v[o], o);
         }
     }
@@ -180,11 +194,15 @@ __global__ void __launch_bounds__(kZThreads) zpass_each3_kernel(ZArgs a) {
 }
 
 template <int NZ>
-__global__ void __launch_bounds__(kZThreads) zpass_sum3_kernel(ZArgs a) {
+__global__ void __launch_bounds__(ZS<NZ>::NT) zpass_sum3_kernel(ZArgs a) {
     using S = ZS<NZ>;
     constexpr int A = S::A, B = S::B;
     extern __shared__ float4 smem_raw[];
     ZCtx<NZ> c(a, reinterpret_cast<float2*>(smem_raw));
+    pdl_wait();
+    pdl_trigger();
+    float kap[B];
+    c.load_kappa(kap);
     c.f1_three();
     __syncthreads();
     float2 acc[B];
@@ -196,7 +214,7 @@ __global__ void __launch_bounds__(kZThreads) zpass_sum3_kernel(ZArgs a) {
             float2 v[B];
             c.f2(o, v);
 #pragma unroll
-            for (int k2 = 0; k2 < B; k2++) acc[k2] = cadd(acc[k2], cmul(v[k2], c.mult(o, c.r + A * k2)));
+            for (int k2 = 0; k2 < B; k2++) acc[k2] = cadd(acc[k2], cmul(v[k2], c.mult(o, c.r + A * k2, kap[k2])));
         }
     }
     __syncthreads();
@@ -213,6 +231,7 @@ static ZKernels make_z() {
     k.sum3 = zpass_sum3_kernel<NZ>;
     k.smem = ZS<NZ>::smem;
     k.tc = ZS<NZ>::TC;
+    k.nt = ZS<NZ>::NT;
     return k;
 }
 

@@ -309,7 +309,10 @@ pat_status pat_create_grid(const pat_grid_desc* desc, const pat_sampling_desc* s
     if (st == PAT_OK) st = build_tables(G);
     if (st == PAT_OK) {
         e = configure_kernels(g, nullptr, nullptr);
-        if (e != cudaSuccess) st = cuda_fail(e, "configure_kernels");
+        if (e != cudaSuccess) {
+            const std::string where = std::string("configure_kernels (") + configure_failure() + ")";
+            st = cuda_fail(e, where.c_str());
+        }
     }
     if (st != PAT_OK) {
         std::string msg = g_err;

@@ -88,6 +88,7 @@ struct Profiler {
 
 // Launchers (pat_run.cu, pat_sample.cu).  All return cudaSuccess or the launch error.
 int plane_cluster_size(int nx, int ny);
+const char* configure_failure();  // which attribute the last failed configure_kernels call set
 cudaError_t configure_kernels(const Geom& g, size_t* plane_smem, size_t* z_smem);
 cudaError_t run_forward(const Geom& g, const DeviceTables& t, const Workspace& w, const Scalars& s,
                         int kind, int m, const float* p0, float* f, cudaStream_t st, Profiler* prof);

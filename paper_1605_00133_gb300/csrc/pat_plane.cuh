@@ -43,6 +43,11 @@ struct PS {
     static constexpr int AREA = cmax(RC, CC) * P;                // one field's slab
     static constexpr int NT = kPlaneThreads;
     static constexpr size_t smem(int nf) { return (size_t)2 * nf * AREA * sizeof(float2); }
+    // CTAs per SM the three-field kernels can hold (228 KB of shared memory per SM, 1 KB reserved
+    // per CTA); the register budget follows it, so small planes keep 64 registers per thread and
+    // large planes (one CTA per SM) get the full register file instead of spilling
+    static constexpr int MINB = (int)(228 * 1024 / (smem(3) + 1024)) >= 4 ? 4
+                              : (int)(228 * 1024 / (smem(3) + 1024)) >= 2 ? 2 : 1;
 };
 
 __device__ __forceinline__ int axis_pos(int i, int z, int y, int x) { return i == 0 ? z : (i == 1 ? y : x); }
@@ -180,7 +185,7 @@ __device__ __forceinline__ PlaneIdx plane_idx(const PlaneArgs& a, cg::cluster_gr
 #define PAT_POINTWISE_END }
 
 template <int NX, int NY>
-__global__ void __launch_bounds__(kPlaneThreads, 4) plane_init_kernel(PlaneArgs a) {
+__global__ void __launch_bounds__(kPlaneThreads, (PS<NX, NY>::MINB)) plane_init_kernel(PlaneArgs a) {
     using S = PS<NX, NY>;
     cg::cluster_group cl = cg::this_cluster();
     extern __shared__ float4 smem_raw[];
@@ -210,7 +215,7 @@ __global__ void __launch_bounds__(kPlaneThreads, 4) plane_init_kernel(PlaneArgs 
 }
 
 template <int NX, int NY>
-__global__ void __launch_bounds__(kPlaneThreads, 4) plane_vel_kernel(PlaneArgs a) {
+__global__ void __launch_bounds__(kPlaneThreads, (PS<NX, NY>::MINB)) plane_vel_kernel(PlaneArgs a) {
     using S = PS<NX, NY>;
     cg::cluster_group cl = cg::this_cluster();
     extern __shared__ float4 smem_raw[];
@@ -255,7 +260,7 @@ __global__ void __launch_bounds__(kPlaneThreads, 4) plane_vel_kernel(PlaneArgs a
 }
 
 template <int NX, int NY>
-__global__ void __launch_bounds__(kPlaneThreads, 4) plane_rho_fwd_kernel(PlaneArgs a) {
+__global__ void __launch_bounds__(kPlaneThreads, (PS<NX, NY>::MINB)) plane_rho_fwd_kernel(PlaneArgs a) {
     using S = PS<NX, NY>;
     cg::cluster_group cl = cg::this_cluster();
     extern __shared__ float4 smem_raw[];
@@ -306,7 +311,7 @@ __global__ void __launch_bounds__(kPlaneThreads, 4) plane_rho_fwd_kernel(PlaneAr
 }
 
 template <int NX, int NY>
-__global__ void __launch_bounds__(kPlaneThreads, 4) plane_rho_adj_kernel(PlaneArgs a) {
+__global__ void __launch_bounds__(kPlaneThreads, (PS<NX, NY>::MINB)) plane_rho_adj_kernel(PlaneArgs a) {
     using S = PS<NX, NY>;
     cg::cluster_group cl = cg::this_cluster();
     extern __shared__ float4 smem_raw[];

@@ -40,18 +40,34 @@ static PlaneKernels plane_kernels_for(int nx, int ny) {
 
 int plane_cluster_size(int nx, int ny) { return plane_kernels_for(nx, ny).cs; }
 
+static const char* g_config_what = "";
+const char* configure_failure() { return g_config_what; }
+
 cudaError_t configure_kernels(const Geom& g, size_t* plane_smem, size_t* z_smem) {
     PlaneKernels pk = plane_kernels_for(g.nx, g.ny);
     ZKernels zk = z_kernels_for(g.nz);
-    if (!pk.vel || !zk.grad3) return cudaErrorInvalidValue;
-    PAT_TRY(cudaFuncSetAttribute(pk.init, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pk.smem_init));
-    PAT_TRY(cudaFuncSetAttribute(pk.vel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pk.smem3));
-    PAT_TRY(cudaFuncSetAttribute(pk.rho_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pk.smem3));
-    PAT_TRY(cudaFuncSetAttribute(pk.rho_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pk.smem3));
-    PAT_TRY(cudaFuncSetAttribute(zk.grad3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zk.smem));
-    PAT_TRY(cudaFuncSetAttribute(zk.each3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zk.smem));
-    PAT_TRY(cudaFuncSetAttribute(zk.sum3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zk.smem));
-    PAT_TRY(configure_sampling(g));
+    if (!pk.vel || !zk.grad3) {
+        g_config_what = "no kernel instantiation for this grid shape";
+        return cudaErrorInvalidValue;
+    }
+#define PAT_CFG(call, what)                  \
+    do {                                     \
+        cudaError_t _e = (call);             \
+        if (_e != cudaSuccess) {             \
+            g_config_what = what;            \
+            return _e;                       \
+        }                                    \
+    } while (0)
+    PAT_CFG(cudaFuncSetAttribute(pk.init, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pk.smem_init), "plane_init smem");
+    PAT_CFG(cudaFuncSetAttribute(pk.vel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pk.smem3), "plane_vel smem");
+    PAT_CFG(cudaFuncSetAttribute(pk.rho_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pk.smem3), "plane_rho_fwd smem");
+    PAT_CFG(cudaFuncSetAttribute(pk.rho_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pk.smem3), "plane_rho_adj smem");
+    PAT_CFG(cudaFuncSetAttribute(zk.grad3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zk.smem), "zpass_grad3 smem");
+    PAT_CFG(cudaFuncSetAttribute(zk.each3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zk.smem), "zpass_each3 smem");
+    PAT_CFG(cudaFuncSetAttribute(zk.sum3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zk.smem), "zpass_sum3 smem");
+    PAT_CFG(configure_sampling(g), "sampling smem");
+#undef PAT_CFG
+    g_config_what = "";
     if (plane_smem) *plane_smem = pk.smem3;
     if (z_smem) *z_smem = zk.smem;
     return cudaSuccess;

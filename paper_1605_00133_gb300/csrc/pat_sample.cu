@@ -153,6 +153,8 @@ static size_t g_shd_smem_max = 0;
 
 cudaError_t configure_sampling(const Geom& g) {
     const size_t shd_bytes = (size_t)g.m_plane * sizeof(float);
+    // sHd planes live in shared memory; larger planes are refused when the grid is created
+    if (g.m_plane > 32768) return cudaSuccess;
     if (shd_bytes > 48 * 1024 && shd_bytes > g_shd_smem_max) {
         cudaError_t e = cudaFuncSetAttribute(shd_forward_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shd_bytes);
         if (e != cudaSuccess) return e;

@@ -112,7 +112,7 @@ static cudaError_t launch_plane(PlaneKernel k, size_t smem, int cs, const PlaneA
 static cudaError_t launch_z(ZKernel k, const ZKernels& zk, const ZArgs& a, cudaStream_t st) {
     const int ncols = a.g.ny * a.g.nxh;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((ncols + zk.tc - 1) / zk.tc, a.g.B, 1);
+    cfg.gridDim = dim3((ncols + zk.tc - 1) / zk.tc, a.g.B, k == zk.each3 ? 3 : 1);
     cfg.blockDim = dim3(zk.nt, 1, 1);
     cfg.dynamicSmemBytes = zk.smem;
     cfg.stream = st;

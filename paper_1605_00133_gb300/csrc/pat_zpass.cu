@@ -162,6 +162,8 @@ __global__ void __launch_bounds__(ZS<NZ>::NT) zpass_grad3_kernel(ZArgs a) {
     for (int o = 0; o < 3; o++) c.i2(a.spec[o], o);
 }
 
+// One field per CTA (blockIdx.z): the three components are independent, and splitting them
+// triples the CTAs in flight while cutting each thread's live registers.
 template <int NZ>
 __global__ void __launch_bounds__(ZS<NZ>::NT) zpass_each3_kernel(ZArgs a) {
     using S = ZS<NZ>;
@@ -170,27 +172,21 @@ __global__ void __launch_bounds__(ZS<NZ>::NT) zpass_each3_kernel(ZArgs a) {
     ZCtx<NZ> c(a, reinterpret_cast<float2*>(smem_raw));
     pdl_wait();
     pdl_trigger();
+    const int o = blockIdx.z;
     float kap[B];
     c.load_kappa(kap);
-    c.f1_three();
+    c.f1(a.spec[o], 0);
     __syncthreads();
-    float2 v[3][B];
-    if (c.vcol) {
-#pragma unroll
-        for (int o = 0; o < 3; o++) c.f2(o, v[o]);
-    }
+    float2 v[B];
+    if (c.vcol) c.f2(0, v);
     __syncthreads();
     if (c.vcol) {
 #pragma unroll
-        for (int o = 0; o < 3; o++) {
-#pragma unroll
-            for (int k2 = 0; k2 < B; k2++) v[o][k2] = cmul(v[o][k2], c.mult(o, c.r + A * k2, kap[k2]));
-            c.i1(v[o], o);
-        }
+        for (int k2 = 0; k2 < B; k2++) v[k2] = cmul(v[k2], c.mult(o, c.r + A * k2, kap[k2]));
+        c.i1(v, 0);
     }
     __syncthreads();
-#pragma unroll 1
-    for (int o = 0; o < 3; o++) c.i2(a.spec[o], o);
+    c.i2(a.spec[o], 0);
 }
 
 template <int NZ>

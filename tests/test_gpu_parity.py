@@ -222,13 +222,23 @@ def test_c2_forward_matches_oracle_reduced_T(oracle_mod, dev):
 
 
 @pytest.mark.slow
-def test_c2_forward_matches_oracle_full_T(oracle_mod, dev):
-    """The headline workload end to end: 64x128x128, T = 400, rSP 12.5 %, vessel phantom."""
+def test_c2_forward_and_adjoint_match_oracle_full_T(oracle_mod, dev):
+    """The headline workload end to end: 64x128x128, T = 400, rSP 12.5 %, vessel phantom.
+    Forward (measured 3.2e-6) and the adjoint of realistic data, C A p0 + 1 % noise (measured
+    3.3e-6), within 1e-5.  The adjoint of white-noise data carries broadband content injected at
+    every step; its FP32 floor grows faster with T (an independent FP32 restatement of the same
+    recurrence with an accurate library FFT gives the same error: 7.2e-6 at T = 100), measured
+    2.3e-5 at T = 400, so that case is held to 4e-5."""
     w = presets.workload("c2")
     g, s = w.grid, w.sampling
     p0 = w.p0()
     op = make_op(g, s)
-    assert rel(gpu_forward(op, p0, dev), oracle_mod.forward(g, s, p0)) < TOL
+    f_ref = oracle_mod.forward(g, s, p0)
+    assert rel(gpu_forward(op, p0, dev), f_ref) < TOL
+    y = synth.add_relative_noise(f_ref, 0.01, 4)
+    assert rel(gpu_adjoint(op, y, dev), oracle_mod.adjoint(g, s, y)) < TOL
+    yw = np.random.default_rng(0).standard_normal((g.T, s.m))
+    assert rel(gpu_adjoint(op, yw, dev), oracle_mod.adjoint(g, s, yw)) < 4e-5
 
 
 # ------------------------------------------------------------------------------ large grid (c4)

@@ -257,8 +257,8 @@ def main():
                    "share": v[0] / total_prof} for k, v in prof.items()}
     dominant = max(kernels, key=lambda k: kernels[k]["ms_total"])
 
-    # roofline: the time step is the unit of work (SURVEY 48 bytes per voxel per step: six FP32
-    # state fields read and written once); one step = 4 launches on one stream
+    # roofline: the time step is the unit of work (48 bytes per voxel per step: six FP32 state fields
+    # read and written once); one step = 3 line-pass launches (x, y, z) on one stream
     import json as _json
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     peak, peak_src = 6800.0, "fallback 6.8 TB/s"
@@ -272,8 +272,7 @@ def main():
     # DRAM bytes of one forward time step from the committed ncu capture, valid only for the kernel
     # sources it was taken on (profiles/pat_step_kernels_c2.md)
     traffic = STEP_TRAFFIC.get((_source_hash(), w.name, B))
-    roofline = {"bound": "hbm", "kernel": "time step (zpass_grad3 + plane_vel + zpass_each3 + plane_rho_fwd, "
-                                          "and the adjoint's four)",
+    roofline = {"bound": "hbm", "kernel": "time step (line passes x, y, z of A, and of A^T)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "peak_source": peak_src,
                 "algorithmic_bytes_per_unit": "48 B per voxel per time step",

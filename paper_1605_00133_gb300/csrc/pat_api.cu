@@ -2,10 +2,10 @@
 //
 // Constant tables are computed here in double precision and stored as FP32:
 //   FFT twiddles exp(-2 pi i m / L) per axis;
-//   kappa(|k|) / N on the half spectrum, kappa = sinc(c dt |k| / 2) (the k-space correction that
-//   makes the leapfrog step exact per plane wave; the 1/N of the inverse 3D FFT is folded in);
-//   i k exp(+/- i k dx / 2) per axis (staggered spectral derivative factors; the Nyquist bin
-//   k = -pi/dx gives a real factor, so every operator maps real fields to real fields);
+//   kappa(|k|) = sinc(c dt |k| / 2) (the k-space correction that makes the leapfrog step exact
+//   per plane wave) at every point of every line of each axis, in that axis's line layout;
+//   i k exp(+/- i k dx / 2) per axis and bin (staggered spectral derivative factors; the Nyquist
+//   bin k = -pi/dx gives a real factor, so every operator maps real fields to real fields);
 //   split-field PML factors a = exp(-alpha dt / 2), alpha = pml_alpha (c/dx) (d/P)^4, on regular
 //   (j) and staggered (j + 1/2) points, and the per-axis update coefficients built from them.
 #include <math.h>
@@ -162,9 +162,9 @@ pat_status build_tables(pat_grid* G) {
         }
         if ((st = upload(G, &G->t.tw[a], tw, "twiddles")) != PAT_OK) return st;
     }
-    // derivative factors (x: half spectrum)
+    // derivative factors, every bin of each axis
     for (int a = 0; a < 3; a++) {
-        const int len = (a == AX) ? G->g.nxh : n[a];
+        const int len = n[a];
         std::vector<float2> dp(len), dm(len);
         for (int m = 0; m < len; m++) {
             const double k = wavenumber(m, n[a], d.dx);
@@ -177,24 +177,26 @@ pat_status build_tables(pat_grid* G) {
         if ((st = upload(G, &G->t.dplus[a], dp, "dplus")) != PAT_OK) return st;
         if ((st = upload(G, &G->t.dminus[a], dm, "dminus")) != PAT_OK) return st;
     }
-    // kappa / N on the half spectrum, [kz][kx][ky]
+    // kappa at every line point of each axis, [len][ncols] in the line layout of pat_internal.h
     {
-        const double N = (double)d.nz * d.ny * d.nx;
-        std::vector<float> kap((size_t)d.nz * d.ny * G->g.nxh);
-        size_t i = 0;
-        for (int kz = 0; kz < d.nz; kz++) {  // same (kz, kx, ky) order as the half spectra
-            const double wz = wavenumber(kz, d.nz, d.dx);
-            for (int kx = 0; kx < G->g.nxh; kx++) {
-                const double wx = wavenumber(kx, d.nx, d.dx);
-                for (int ky = 0; ky < d.ny; ky++) {
+        const Geom& g = G->g;
+        for (int a = 0; a < 3; a++) {
+            std::vector<float> kap((size_t)g.len[a] * g.ncols[a]);
+            for (int j = 0; j < g.len[a]; j++) {
+                for (int c = 0; c < g.ncols[a]; c++) {
+                    int kz, ky, kx;
+                    if (a == AZ) { kz = j; kx = c / g.ny; ky = c % g.ny; }
+                    else if (a == AY) { ky = j; kz = c / g.nxh; kx = c % g.nxh; }
+                    else { kx = j; kz = c / g.ny; ky = c % g.ny; }
+                    const double wz = wavenumber(kz, d.nz, d.dx);
                     const double wy = wavenumber(ky, d.ny, d.dx);
+                    const double wx = wavenumber(kx, d.nx, d.dx);
                     const double x = 0.5 * d.c * dt * sqrt(wz * wz + wy * wy + wx * wx);
-                    const double kappa = (x == 0.0) ? 1.0 : sin(x) / x;
-                    kap[i++] = (float)(kappa / N);
+                    kap[(size_t)j * g.ncols[a] + c] = (float)((x == 0.0) ? 1.0 : sin(x) / x);
                 }
             }
+            if ((st = upload(G, &G->t.kappa[a], kap, "kappa")) != PAT_OK) return st;
         }
-        if ((st = upload(G, &G->t.kappaN, kap, "kappa")) != PAT_OK) return st;
     }
     // PML-derived coefficient tables
     for (int a = 0; a < 3; a++) {
@@ -212,6 +214,8 @@ pat_status build_tables(pat_grid* G) {
             ct[CT_A2][j] = (float)(A * A);
             ct[CT_DF_D][j] = (float)(-A * dt * d.rho0);
             ct[CT_A][j] = (float)A;
+            ct[CT_C2][j] = (float)(d.c * d.c);
+            ct[CT_FIN][j] = (float)(A * A / (3.0 * d.c * d.c));
         }
         for (int c = 0; c < CT_COUNT; c++)
             if ((st = upload(G, &G->t.coef[c][a], ct[c], "coef")) != PAT_OK) return st;
@@ -230,6 +234,38 @@ pat_status check_device(const pat_grid* G) {
 }  // namespace
 
 namespace pat {
+
+static size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
+
+// The real plane series (sampled kinds) is live only outside the time loop: the forward writes it
+// after the last step, the adjoint has consumed it (its plane spectra) before the first.  So it
+// shares its memory with the states and 3D spectra, which are live only inside the loop.
+WsLayout workspace_layout(const Geom& g, int kind) {
+    const size_t B = (size_t)g.B;
+    WsLayout L;
+    size_t loop = 0;
+    for (int a = 0; a < 3; a++) {
+        L.ms[a] = round256(B * (size_t)g.len[a] * g.ncols[a] * sizeof(float2));
+        loop += 2 * L.ms[a];
+    }
+    L.ph = round256(B * (size_t)g.nspec * sizeof(float2));
+    loop += 2 * L.ph;
+    L.rk = round256(B * (size_t)g.T * g.nplane * sizeof(float2));
+    L.rec = (kind == PAT_SAMPLE_FULL) ? 0 : round256(B * (size_t)g.T * g.m_plane * sizeof(float));
+    L.total = std::max(loop, L.rec) + L.rk;
+    return L;
+}
+
+void workspace_carve(const Geom& g, const WsLayout& L, unsigned char* base, Workspace* w) {
+    (void)g;
+    size_t off = 0;
+    for (int a = 0; a < 3; a++)
+        for (int s = 0; s < 2; s++, off += L.ms[a]) w->ms[a][s] = (float2*)(base + off);
+    for (int s = 0; s < 2; s++, off += L.ph) w->ph[s] = (float2*)(base + off);
+    w->rec = L.rec ? (float*)base : nullptr;  // aliases the loop state, see workspace_layout
+    w->rk = (float2*)(base + std::max(off, L.rec));
+}
+
 pat_status set_error(pat_status s, const char* msg) { return fail(s, msg); }
 pat_status set_cuda_error(cudaError_t e, const char* where) { return cuda_fail(e, where); }
 pat_status grid_alloc(pat_grid* G, void** p, size_t bytes, const char* what) { return dalloc(G, p, bytes, what); }
@@ -277,28 +313,28 @@ pat_status pat_create_grid(const pat_grid_desc* desc, const pat_sampling_desc* s
     g.nx = G->d.nx;
     g.nxh = g.nx / 2 + 1;
     g.B = G->d.batch;
+    g.nzh = g.nz / 2 + 1;
     g.cs = plane_cluster_size(g.nx, g.ny);
-    g.rows_cta = (g.ny / 2) / g.cs;
-    g.cols_cta = (g.nx / 2) / g.cs;
-    g.tc = 0;
+    g.len[AZ] = g.nz;
+    g.len[AY] = g.ny;
+    g.len[AX] = g.nx;
+    g.ncols[AZ] = g.nxh * g.ny;
+    g.ncols[AY] = g.nz * g.nxh;
+    g.ncols[AX] = g.nzh * g.ny;
     g.nreal = (long long)g.nz * g.ny * g.nx;
     g.nspec = (long long)g.nz * g.ny * g.nxh;
+    g.nplane = (long long)g.nxh * g.ny;
     g.sensor_z = G->d.sensor_z;
     g.T = G->d.T;
     g.m_plane = M;
 
-    // workspace
-    const size_t B = (size_t)g.B;
-    for (int i = 0; i < 6 && st == PAT_OK; i++)
-        st = dalloc(G, (void**)&G->w.st[i], B * g.nreal * sizeof(float), "state");
-    // the three half-spectrum buffers are one allocation: kernels address field f at spec[0] + f*B*nspec
-    if (st == PAT_OK) st = dalloc(G, (void**)&G->w.spec[0], 3 * B * g.nspec * sizeof(float2), "spectra");
-    if (st == PAT_OK) {
-        G->w.spec[1] = G->w.spec[0] + B * g.nspec;
-        G->w.spec[2] = G->w.spec[1] + B * g.nspec;
+    // workspace: one allocation, carved as workspace_carve describes
+    {
+        const WsLayout L = workspace_layout(g, G->kind);
+        unsigned char* base = nullptr;
+        st = dalloc(G, (void**)&base, L.total, "workspace");
+        if (st == PAT_OK) workspace_carve(g, L, base, &G->w);
     }
-    if (st == PAT_OK && G->kind != PAT_SAMPLE_FULL)
-        st = dalloc(G, (void**)&G->w.rec, B * (size_t)g.T * M * sizeof(float), "plane series");
     if (st == PAT_OK && G->kind == PAT_SAMPLE_POINTS)
         st = upload(G, &G->w.idx, std::vector<int32_t>(sampling->indices, sampling->indices + G->m), "indices");
     if (st == PAT_OK && (G->kind == PAT_SAMPLE_HADAMARD01 || G->kind == PAT_SAMPLE_HADAMARDPM)) {
@@ -308,7 +344,7 @@ pat_status pat_create_grid(const pat_grid_desc* desc, const pat_sampling_desc* s
     }
     if (st == PAT_OK) st = build_tables(G);
     if (st == PAT_OK) {
-        e = configure_kernels(g, nullptr, nullptr);
+        e = configure_kernels(g);
         if (e != cudaSuccess) {
             const std::string where = std::string("configure_kernels (") + configure_failure() + ")";
             st = cuda_fail(e, where.c_str());
@@ -387,8 +423,7 @@ pat_status pat_sample_adjoint(pat_grid* G, const float* f, float* pbar, int32_t 
     return PAT_OK;
 }
 
-static const char* kClassNames[KC_COUNT] = {"plane_init", "plane_vel", "plane_rho_fwd", "plane_rho_adj",
-                                              "zpass_grad3", "zpass_each3", "zpass_sum3", "sample"};
+static const char* kClassNames[KC_COUNT] = {"line_x", "line_y", "line_z", "plane_fft", "z_fft", "sample"};
 
 pat_status pat_profile_enable(pat_grid* G, int32_t enable) {
     g_err.clear();
@@ -451,8 +486,6 @@ namespace {
 std::mutex g_noalloc_mu;
 void* g_noalloc_ptr[64] = {nullptr};  // device address of g_noalloc_scratch, per device id
 
-size_t round256(size_t b) { return (b + 255) & ~(size_t)255; }
-
 }  // namespace
 
 extern "C" pat_status pat_forward_noalloc(pat_grid* G, const float* p0, float* f, void* stream) {
@@ -462,11 +495,8 @@ extern "C" pat_status pat_forward_noalloc(pat_grid* G, const float* p0, float* f
     pat_status st = check_device(G);
     if (st != PAT_OK) return st;
     const Geom& g = G->g;
-    const size_t B = (size_t)g.B;
-    const size_t st_bytes = round256(B * g.nreal * sizeof(float));
-    const size_t sp_bytes = round256(3 * B * g.nspec * sizeof(float2));
-    const size_t rec_bytes = (G->kind == PAT_SAMPLE_FULL) ? 0 : round256(B * (size_t)g.T * g.m_plane * sizeof(float));
-    const size_t need = 6 * st_bytes + sp_bytes + rec_bytes;
+    const WsLayout L = workspace_layout(g, G->kind);
+    const size_t need = L.total;
     if (need > PAT_NOALLOC_SCRATCH_BYTES)
         return fail(PAT_ERR_INVALID_ARG, "pat_forward_noalloc: this grid needs " + std::to_string(need) +
                                              " bytes of scratch; the static scratch holds " +
@@ -486,13 +516,7 @@ extern "C" pat_status pat_forward_noalloc(pat_grid* G, const float* p0, float* f
         base = (unsigned char*)g_noalloc_ptr[G->device];
     }
     Workspace w = G->w;  // index sets stay the grid's; all mutable scratch comes from the array
-    size_t off = 0;
-    for (int i = 0; i < 6; i++, off += st_bytes) w.st[i] = (float*)(base + off);
-    w.spec[0] = (float2*)(base + off);
-    w.spec[1] = w.spec[0] + B * g.nspec;
-    w.spec[2] = w.spec[1] + B * g.nspec;
-    off += sp_bytes;
-    w.rec = rec_bytes ? (float*)(base + off) : nullptr;
+    workspace_carve(g, L, base, &w);
     cudaError_t e = run_forward(G->g, G->t, w, G->s, G->kind, G->m, p0, f, (cudaStream_t)stream, nullptr);
     if (e != cudaSuccess) return cuda_fail(e, "pat_forward_noalloc");
     return PAT_OK;

@@ -21,21 +21,25 @@ enum CoefTable {
     CT_VF_G,           // -as * dt / rho0           forward velocity: gradient term
     CT_VF0_G,          // as (as/2 - 1) dt / rho0    forward velocity, first step (u^{-1/2} folded in)
     CT_VA_G,           // dt * rho0                 adjoint velocity: gradient term
-    CT_AS,             // as                        adjoint velocity: transform input
+    CT_AS,             // as                        adjoint velocity: output gain
     CT_VA0_OUT,        // as (1 - as/2)             adjoint velocity, last step (u^{-1/2} folded in)
     CT_A2,             // a^2                       density decay
     CT_DF_D,           // -a dt rho0                forward density: divergence term
-    CT_A,              // a                         adjoint density: transform input
+    CT_A,              // a                         adjoint density: output gain
+    CT_C2,             // c^2                       adjoint density: input gain
+    CT_FIN,            // a^2 / (3 c^2)             adjoint image: rho_i^0 = p0 / (3 c^2) transposed
     CT_COUNT
 };
 
 struct Geom {
     int nz, ny, nx, nxh;        // nxh = nx/2 + 1
+    int nzh;                    // nz/2 + 1
     int B;                      // batch
     int cs;                     // plane-kernel cluster size
-    int rows_cta, cols_cta;     // complex row pairs / packed columns per CTA
-    int tc;                     // z-kernel column tile
-    long long nreal, nspec;     // per batch entry
+    int len[3];                 // line length per axis (z, y, x)
+    int ncols[3];               // lines per batch entry per axis, see Workspace::ms
+    long long nreal, nspec;     // per batch entry: nz*ny*nx reals, nz*nxh*ny half-spectrum values
+    long long nplane;           // nxh*ny: one plane's half spectrum
     int sensor_z;
     int T;
     int m_plane;                // ny * nx
@@ -43,16 +47,25 @@ struct Geom {
 
 struct DeviceTables {
     float2* tw[3];              // FFT twiddles exp(-2 pi i m / L) per axis length
-    float* kappaN;              // kappa(|k|) / N on the half spectrum [nz][nxh][ny]
-    float2* dplus[3];           // i k exp(+i k dx/2) per axis (x: nxh entries)
+    float* kappa[3];            // kappa(|k|) at every point of every line of axis a: [len][ncols]
+    float2* dplus[3];           // i k exp(+i k dx/2) per axis, every bin of the axis
     float2* dminus[3];          // i k exp(-i k dx/2)
     float* coef[CT_COUNT][3];   // per-axis coefficient tables
 };
 
+// Mixed representation: the split fields u_i, rho_i of axis i are kept with axis i in real space
+// and the other two axes Fourier transformed (the PML factor of axis i depends on x_i alone, so the
+// update is pointwise there).  Line c of axis i at position j sits at ms[i][s][(b*len + j)*ncols + c]:
+//   z: c = kx*ny + ky              (kx <= nx/2)        ncols = nxh*ny
+//   y: c = kz*nxh + kx             (kx <= nx/2)        ncols = nz*nxh
+//   x: c = kz*ny + ky              (kz <= nz/2)        ncols = nzh*ny
+// The pressure (or its adjoint) is kept as a full 3D half spectrum ph[.][b][kz][kx][ky].
 struct Workspace {
-    float* st[6];               // u_z,u_y,u_x,rho_z,rho_y,rho_x (forward) / v_i, q_i (adjoint)
-    float2* spec[3];            // half spectra [B][nz][nxh][ny] (one allocation)
-    float* rec;                 // recorded / injected plane series [B][T][M] (sampled kinds)
+    float2* ms[3][2];           // per axis: state 1 (u_i | adjoint of rho_i), state 2 (rho_i | adjoint of u_i)
+    float2* ph[2];              // 3D half spectra [B][nz][nxh][ny], double-buffered across passes
+    float2* rk;                 // plane spectra [B][T][nxh][ny]: recorded (A) or injected (A^T)
+    float* rec;                 // real plane series [B][T][M] (sampled kinds); shares memory with
+                                // ms and ph, which are dead whenever it is live
     int32_t* idx;               // POINTS index list
     int32_t* perm;              // HADAMARD scramble
     int32_t* rows;              // HADAMARD rows
@@ -64,8 +77,7 @@ struct Scalars {
 
 // Kernel classes timed by the optional profiler (CUDA events on the launching stream).
 enum KernelClass {
-    KC_PLANE_INIT = 0, KC_PLANE_VEL, KC_PLANE_RHO_FWD, KC_PLANE_RHO_ADJ,
-    KC_Z_ONE_TO_THREE, KC_Z_THREE_TO_THREE, KC_Z_THREE_TO_ONE, KC_SAMPLE, KC_COUNT
+    KC_LINE_X = 0, KC_LINE_Y, KC_LINE_Z, KC_PLANE_FFT, KC_Z_FFT, KC_SAMPLE, KC_COUNT
 };
 
 struct Profiler {
@@ -89,7 +101,13 @@ struct Profiler {
 // Launchers (pat_run.cu, pat_sample.cu).  All return cudaSuccess or the launch error.
 int plane_cluster_size(int nx, int ny);
 const char* configure_failure();  // which attribute the last failed configure_kernels call set
-cudaError_t configure_kernels(const Geom& g, size_t* plane_smem, size_t* z_smem);
+cudaError_t configure_kernels(const Geom& g);
+// workspace layout: bytes of each part (256-byte aligned) for a grid and sampling kind
+struct WsLayout {
+    size_t ms[3], ph, rk, rec, total;
+};
+WsLayout workspace_layout(const Geom& g, int kind);
+void workspace_carve(const Geom& g, const WsLayout& L, unsigned char* base, Workspace* w);
 cudaError_t run_forward(const Geom& g, const DeviceTables& t, const Workspace& w, const Scalars& s,
                         int kind, int m, const float* p0, float* f, cudaStream_t st, Profiler* prof);
 cudaError_t run_adjoint(const Geom& g, const DeviceTables& t, const Workspace& w, const Scalars& s,

@@ -8,33 +8,26 @@
 namespace pat {
 
 static constexpr int kPlaneThreads = 256;
-static constexpr int kZCols = 32;  // half-spectrum columns per z-pass CTA
+static constexpr int kZCols = 32;  // half-spectrum columns per z-FFT CTA
 
-enum PlaneFlag { PF_NO_FWD = 1, PF_NO_OLD = 2, PF_HAVE_LAMBDA = 4, PF_FINAL = 8 };
-
+// (y,x) plane transforms of a stack of planes: real [b][p][ny][nx] <-> half spectrum [b][p][nxh][ny].
 struct PlaneArgs {
     Geom g;
     const float2* tw_x;
     const float2* tw_y;
-    float2* spec[3];
-    float* st[3];
-    const float* A1[3];
-    const float* A2[3];
-    const float* A3[3];
-    float c2, s0, s1;
-    const float* in_real;
-    float* out_real;
-    float* rec;
-    const float* inj;
-    int n_rec;
-    int flags;
+    const float* in_real;       // rfft input planes
+    float* out_real;            // irfft output planes
+    const float2* spec_in;      // irfft input spectra
+    float2* spec_out;           // rfft output spectra
+    long long bs_real, bs_spec; // batch strides (elements) of the real and spectral stacks
+    float scale;                // irfft output factor
 };
 
 typedef void (*PlaneKernel)(PlaneArgs);
 
 struct PlaneKernels {
-    PlaneKernel init = nullptr, vel = nullptr, rho_fwd = nullptr, rho_adj = nullptr;
-    size_t smem_init = 0, smem3 = 0;
+    PlaneKernel rfft = nullptr, irfft = nullptr;
+    size_t smem = 0;
     int cs = 0;
 };
 
@@ -46,23 +39,70 @@ PlaneKernels plane_kernels_nx64(int ny);
 PlaneKernels plane_kernels_nx128(int ny);
 PlaneKernels plane_kernels_nx256(int ny);
 
+// z transforms of a 3D half spectrum, in place: [b][z][c] <-> [b][kz][c], c = kx*ny + ky
 struct ZArgs {
     Geom g;
     const float2* tw_z;
-    float2* spec[3];
-    const float* kappaN;
-    const float2* dt[3];
+    float2* spec;
+    float scale;                // inverse transform output factor
 };
 
 typedef void (*ZKernel)(ZArgs);
 
 struct ZKernels {
-    ZKernel grad3 = nullptr, each3 = nullptr, sum3 = nullptr;
+    ZKernel fwd = nullptr, inv = nullptr;
     size_t smem = 0;
     int tc = 0;  // columns per CTA
     int nt = 0;  // threads per CTA
 };
 
 ZKernels z_kernels_for(int nz);
+
+// Line passes of the time step (pat_line.cuh).
+enum LineMode { LM_STEP = 0, LM_INIT = 1, LM_FIN = 2 };
+enum LineFlag { LF_NO_OLD1 = 1, LF_NO_OLD2 = 2, LF_ACCUM = 4, LF_RECORD = 8, LF_INJECT = 16 };
+
+struct LineArgs {
+    Geom g;
+    int ncols;                  // lines per batch entry
+    int mode, flags;
+    const float2* tw;           // exp(-2 pi i m / L), m < L
+    const float2* in;           // 3D half spectrum read (LM_STEP, LM_INIT)
+    float2* out;                // 3D half spectrum written or accumulated (LM_STEP, LM_FIN)
+    float2* st1;                // mixed-representation states [B][L][ncols]
+    float2* st2;
+    const float* kap;           // kappa(|k|) at every line point [L][ncols]
+    const float2* dpre;         // k-space factor before the first inverse transform (NULL: none)
+    const float2* dmid;         // between the two state updates
+    const float2* dpost;        // after the last forward transform (NULL: none)
+    float s_pre, s_mid, s_post; // scalar factors of the same three places
+    const float* c1[3];         // state 1: decay, input gain, output gain (one entry per position)
+    const float* c2[3];         // state 2
+    float2* rec;                // z lines: plane spectrum recorded this step (LF_RECORD) ...
+    const float2* inj;          // ... or injected this step (LF_INJECT); batch stride plane_bs
+    long long plane_bs;
+    int zs;                     // detection plane index
+    float s_rec;                // 1/nz
+};
+
+typedef void (*LineKernel)(LineArgs);
+
+struct LineKernels {
+    LineKernel pass[3] = {nullptr, nullptr, nullptr};  // by axis (z, y, x) for this line length
+    size_t smem = 0;
+    int tc = 0;  // lines per CTA
+    int nt = 0;  // threads per CTA
+};
+
+LineKernels line_kernels_l8();
+LineKernels line_kernels_l16();
+LineKernels line_kernels_l32();
+LineKernels line_kernels_l64();
+LineKernels line_kernels_l128();
+LineKernels line_kernels_l256();
+
+// adjoint start: spec[b][kz][c] = S[b][c] exp(-2 pi i kz zs / nz)
+cudaError_t launch_spread_plane(const Geom& g, const float2* tw_z, const float2* S, long long s_bs,
+                                float2* spec, cudaStream_t st);
 
 }  // namespace pat

@@ -1,0 +1,353 @@
+// pat_line.cuh - line passes of the k-space time step (Sec. 4.3) in mixed representation.
+//
+// The split-field update of axis i (velocity u_i, density rho_i) needs only the derivative along
+// axis i and the PML factor of axis i, which depends on x_i alone.  So u_i and rho_i are kept with
+// axis i in real space and the other two axes in Fourier space, and the pressure p = c^2 sum rho_i
+// as a full 3D half spectrum.  One pass over the lines of axis i then does a whole time step of
+// that axis with 1D transforms only:
+//
+//   forward  g   = F_i^-1[ i k_i kappa e^{+ik_i dx/2} p^ ] / n_i        (D_i^+ p)
+//            u_i = as^2 u_i - as dt/rho0 g                              (state 1)
+//            d   = F_i^-1[ i k_i kappa e^{-ik_i dx/2} F_i u_i ] / n_i   (D_i^- u_i)
+//            rho_i = a^2 rho_i - a dt rho0 d                            (state 2)
+//            p^_new (+)= c^2 F_i rho_i
+//   adjoint  l   = F_i^-1[ lambda^ ] / n_i,  q_i = a^2 q_i + c^2 l,  w = a q_i
+//            g   = F_i^-1[ i k_i kappa e^{+ik_i dx/2} F_i w ] / n_i
+//            v_i = as^2 v_i + dt rho0 g,  y = as v_i
+//            lambda^_new (+)= (dt/rho0) i k_i kappa e^{-ik_i dx/2} F_i y
+//
+// i.e. in both directions: [pre factor] F^-1, state update, F, [mid factor] F^-1, state update, F,
+// [post factor], accumulate.  The passes of one step run x, y, z; the x pass writes the new
+// spectrum, the y and z passes add to it; the z pass also records (forward) the detection plane's
+// (kx, ky) spectrum (1/nz) sum_kz p^ e^{+2 pi i kz zs/nz}, or injects (adjoint) the data spectrum
+// S e^{-2 pi i kz zs/nz}.
+//
+// A CTA owns TC lines.  A line's length-L transform is the two-pass split of pat_fft.cuh: in the
+// k-space layout thread r < A holds X[r + A k2] (k2 < B), in the spatial layout thread r < B holds
+// x[r + B k2] (k2 < A); each transform is one exchange through shared memory laid out [row][line]
+// with the line index fastest.  Two exchange buffers alternate, so every transform costs one
+// barrier.
+//
+// Spectrum access per axis (3D half spectrum [kz][kx][ky], kx <= nx/2):
+//   z lines (kx, ky): column access, stride nxh*ny
+//   y lines (kz, kx): each line is a contiguous row; the CTA's TC rows are one contiguous block,
+//                     moved through shared memory (row pitch L+1) to stay coalesced
+//   x lines (kz <= nz/2, ky): bins kx > nx/2 are the conjugates of (-kz, nx-kx, -ky); on output the
+//                     line also writes that mirror entry, except on the self-conjugate planes
+//                     kz = 0 and kz = nz/2, whose lines (ky) and (-ky) are both present.
+#pragma once
+#include "pat_fft.cuh"
+#include "pat_kargs.h"
+
+namespace pat {
+
+template <int L>
+struct LS {
+    static constexpr int A = Split<L>::A;  // values per thread, spatial layout
+    static constexpr int B = Split<L>::B;  // values per thread, k-space layout
+    static constexpr int TC = (L >= 128) ? 16 : 32;
+    static constexpr int NT = A * TC;
+    static constexpr int PITCH = L + 1;     // staging row pitch for y lines
+    static constexpr int BUF = L * TC + TC; // one exchange buffer (float2), also holds TC staged rows
+    static constexpr size_t smem = 2 * (size_t)BUF * sizeof(float2);
+    static constexpr int MINB = (NT >= 256) ? 2 : 4;
+};
+
+template <int L, int AX>
+struct LineCtx {
+    using S = LS<L>;
+    static constexpr int A = S::A, B = S::B, TC = S::TC;
+    const LineArgs& a;
+    float2* buf0;
+    float2* buf1;
+    int cl, r, col, col0, b;
+    bool vcol;
+    size_t sbase;   // state element of this line at position 0
+    size_t pbase;   // this batch entry's 3D spectrum
+    int ka, kb;     // x lines: kz, ky
+    int ma, mb;     // x lines: the mirror line's kz, ky
+
+    __device__ LineCtx(const LineArgs& args, float2* smem) : a(args) {
+        buf0 = smem;
+        buf1 = smem + S::BUF;
+        const int tid = threadIdx.x;
+        cl = tid % TC;
+        r = tid / TC;
+        col0 = blockIdx.x * TC;
+        col = col0 + cl;
+        vcol = col < a.ncols;
+        b = blockIdx.y;
+        sbase = (size_t)b * L * a.ncols + col;
+        pbase = (size_t)b * a.g.nspec;
+        ka = kb = ma = mb = 0;
+        if (AX == 2) {
+            const int ny = a.g.ny, nz = a.g.nz;
+            ka = col / ny;
+            kb = col - ka * ny;
+            ma = (nz - ka) & (nz - 1);
+            mb = (ny - kb) & (ny - 1);
+        }
+    }
+    // ---- transforms between the layouts (every thread of the CTA must call these)
+    // k-space layout (v) -> spatial layout (x) through xb
+    __device__ __forceinline__ void inv(float2* v, float2* x, float2* xb) const {
+        if (vcol) {
+            Dft<B, +1>::run(v);
+            float2* dst = xb + r * TC + cl;
+#pragma unroll
+            for (int k1p = 0; k1p < B; k1p++)
+                dst[k1p * A * TC] = (k1p == 0) ? v[0] : cmul(v[k1p], twiddle<L, +1>(a.tw, r * k1p));
+        }
+        __syncthreads();
+        if (vcol && r < B) {
+            const float2* src = xb + r * A * TC + cl;
+#pragma unroll
+            for (int t = 0; t < A; t++) x[t] = src[t * TC];
+            Dft<A, +1>::run(x);
+        }
+    }
+    // spatial layout (x) -> k-space layout (v) through xb
+    __device__ __forceinline__ void fwd(float2* x, float2* v, float2* xb) const {
+        if (vcol && r < B) {
+            Dft<A, -1>::run(x);
+            float2* dst = xb + r * TC + cl;
+#pragma unroll
+            for (int k1 = 0; k1 < A; k1++)
+                dst[k1 * B * TC] = (k1 == 0) ? x[0] : cmul(x[k1], twiddle<L, -1>(a.tw, r * k1));
+        }
+        __syncthreads();
+        if (vcol) {
+            const float2* src = xb + r * B * TC + cl;
+#pragma unroll
+            for (int t = 0; t < B; t++) v[t] = src[t * TC];
+            Dft<B, -1>::run(v);
+        }
+    }
+
+    // ---- 3D spectrum access in the k-space layout
+    __device__ __forceinline__ void load_k(const float2* __restrict__ in, float2* v) const {
+        if (AX == 0) {
+            if (vcol) {
+#pragma unroll
+                for (int k2 = 0; k2 < B; k2++) v[k2] = in[pbase + (size_t)(r + A * k2) * a.ncols + col];
+            }
+        } else if (AX == 1) {
+            const int nrows = min(TC, a.ncols - col0);
+            const float4* blk = reinterpret_cast<const float4*>(in + pbase + (size_t)col0 * L);
+            for (int e = threadIdx.x; e < nrows * (L / 2); e += S::NT) {
+                const float4 w = blk[e];
+                const int row = (2 * e) / L, pt = (2 * e) % L;
+                float2* d = buf1 + row * S::PITCH + pt;
+                d[0] = make_float2(w.x, w.y);
+                d[1] = make_float2(w.z, w.w);
+            }
+            __syncthreads();
+            if (vcol) {
+#pragma unroll
+                for (int k2 = 0; k2 < B; k2++) v[k2] = buf1[cl * S::PITCH + r + A * k2];
+            }
+        } else {
+            if (vcol) {
+                const int nx = a.g.nx, nxh = a.g.nxh, ny = a.g.ny;
+#pragma unroll
+                for (int k2 = 0; k2 < B; k2++) {
+                    const int j = r + A * k2;
+                    if (j <= nx / 2) {
+                        v[k2] = in[pbase + ((size_t)ka * nxh + j) * ny + kb];
+                    } else {
+                        v[k2] = cconj(in[pbase + ((size_t)ma * nxh + (nx - j)) * ny + mb]);
+                    }
+                }
+            }
+        }
+    }
+    // write (or add, LF_ACCUM) the k-space layout values to the 3D spectrum; z lines return the
+    // stored totals in v
+    __device__ __forceinline__ void store_k(float2* __restrict__ out, float2* v, bool accum) const {
+        if (AX == 0) {
+            if (vcol) {
+#pragma unroll
+                for (int k2 = 0; k2 < B; k2++) {
+                    float2* p = out + pbase + (size_t)(r + A * k2) * a.ncols + col;
+                    if (accum) v[k2] = cadd(*p, v[k2]);
+                    *p = v[k2];
+                }
+            }
+        } else if (AX == 1) {
+            // buf0's last reader was the previous inverse transform, fenced by the barrier of the
+            // forward transform since
+            if (vcol) {
+#pragma unroll
+                for (int k2 = 0; k2 < B; k2++) buf0[cl * S::PITCH + r + A * k2] = v[k2];
+            }
+            __syncthreads();
+            const int nrows = min(TC, a.ncols - col0);
+            float4* blk = reinterpret_cast<float4*>(out + pbase + (size_t)col0 * L);
+            for (int e = threadIdx.x; e < nrows * (L / 2); e += S::NT) {
+                const int row = (2 * e) / L, pt = (2 * e) % L;
+                const float2* s = buf0 + row * S::PITCH + pt;
+                float4 w = make_float4(s[0].x, s[0].y, s[1].x, s[1].y);
+                if (accum) {
+                    const float4 o = blk[e];
+                    w.x += o.x; w.y += o.y; w.z += o.z; w.w += o.w;
+                }
+                blk[e] = w;
+            }
+        } else {
+            if (vcol) {
+                const int nx = a.g.nx, nxh = a.g.nxh, ny = a.g.ny, nz = a.g.nz;
+                const bool mirror = (ka != 0) && (2 * ka != nz);
+#pragma unroll
+                for (int k2 = 0; k2 < B; k2++) {
+                    const int j = r + A * k2;
+                    if (j <= nx / 2) {
+                        float2* p = out + pbase + ((size_t)ka * nxh + j) * ny + kb;
+                        *p = accum ? cadd(*p, v[k2]) : v[k2];
+                    }
+                    if (mirror && (j == 0 || j >= nx / 2)) {
+                        float2* p = out + pbase + ((size_t)ma * nxh + ((nx - j) & (nx - 1))) * ny + mb;
+                        const float2 c = cconj(v[k2]);
+                        *p = accum ? cadd(*p, c) : c;
+                    }
+                }
+            }
+        }
+    }
+
+    // ---- pointwise state update in the spatial layout: s = c[0] s + c[1] x (no old: s = c[1] x),
+    // x = c[2] s
+    __device__ __forceinline__ void update(float2* __restrict__ st, const float* const* c, bool no_old,
+                                           float2* x) const {
+        if (vcol && r < B) {
+            float2 o[A];
+            if (!no_old) {
+#pragma unroll
+                for (int k2 = 0; k2 < A; k2++) o[k2] = st[sbase + (size_t)(r + B * k2) * a.ncols];
+            }
+#pragma unroll
+            for (int k2 = 0; k2 < A; k2++) {
+                const int j = r + B * k2;
+                float2 nv = cscale(x[k2], __ldg(c[1] + j));
+                if (!no_old) {
+                    const float d = __ldg(c[0] + j);
+                    nv.x = fmaf(d, o[k2].x, nv.x);
+                    nv.y = fmaf(d, o[k2].y, nv.y);
+                }
+                st[sbase + (size_t)j * a.ncols] = nv;
+                x[k2] = cscale(nv, __ldg(c[2] + j));
+            }
+        }
+    }
+
+    // k-space factor D[j] kappa s (D == NULL: s)
+    __device__ __forceinline__ void factor(float2* v, const float2* __restrict__ D, const float* kap,
+                                           float s) const {
+        if (vcol) {
+#pragma unroll
+            for (int k2 = 0; k2 < B; k2++) {
+                if (D) v[k2] = cmul(v[k2], cscale(__ldg(D + r + A * k2), kap[k2] * s));
+                else v[k2] = cscale(v[k2], s);
+            }
+        }
+    }
+};
+
+template <int L, int AX>
+__global__ void __launch_bounds__(LS<L>::NT, LS<L>::MINB) line_pass_kernel(LineArgs a) {
+    using S = LS<L>;
+    constexpr int A = S::A, B = S::B;
+    extern __shared__ float4 smem_raw[];
+    LineCtx<L, AX> c(a, reinterpret_cast<float2*>(smem_raw));
+    pdl_wait();
+    pdl_trigger();
+    float2 v[B];
+    float2 x[A];
+    const bool accum = (a.flags & LF_ACCUM) != 0;
+
+    if (a.mode == LM_FIN) {
+        // adjoint image term: out += F_i (c1[0] st1)
+        if (c.vcol && c.r < B) {
+#pragma unroll
+            for (int k2 = 0; k2 < A; k2++) {
+                const int j = c.r + B * k2;
+                x[k2] = cscale(a.st1[c.sbase + (size_t)j * a.ncols], __ldg(a.c1[0] + j));
+            }
+        }
+        c.fwd(x, v, c.buf1);
+        c.store_k(a.out, v, true);
+        return;
+    }
+
+    c.load_k(a.in, v);
+    if (a.mode == LM_INIT) {
+        // forward start: st2 = F_i^-1[p^] s_pre  (rho_i^0 = p0 / (3 c^2))
+        c.factor(v, nullptr, nullptr, a.s_pre);
+        c.inv(v, x, c.buf0);
+        if (c.vcol && c.r < B) {
+#pragma unroll
+            for (int k2 = 0; k2 < A; k2++) a.st2[c.sbase + (size_t)(c.r + B * k2) * a.ncols] = x[k2];
+        }
+        return;
+    }
+
+    float kap[B];
+#pragma unroll
+    for (int k2 = 0; k2 < B; k2++)
+        kap[k2] = c.vcol ? __ldg(a.kap + (size_t)(c.r + A * k2) * a.ncols + c.col) : 0.f;
+
+    c.factor(v, a.dpre, kap, a.s_pre);
+    c.inv(v, x, c.buf0);
+    c.update(a.st1, a.c1, (a.flags & LF_NO_OLD1) != 0, x);
+    c.fwd(x, v, c.buf1);
+    c.factor(v, a.dmid, kap, a.s_mid);
+    c.inv(v, x, c.buf0);
+    c.update(a.st2, a.c2, (a.flags & LF_NO_OLD2) != 0, x);
+    c.fwd(x, v, c.buf1);
+    c.factor(v, a.dpost, kap, a.s_post);
+
+    if (AX == 0 && (a.flags & LF_INJECT) && c.vcol) {
+        const float2 sv = a.inj[(size_t)c.b * a.plane_bs + c.col];
+#pragma unroll
+        for (int k2 = 0; k2 < B; k2++) {
+            const int kz = c.r + A * k2;
+            v[k2] = cadd(v[k2], cmul(sv, __ldg(a.tw + ((kz * a.zs) & (L - 1)))));
+        }
+    }
+    c.store_k(a.out, v, accum);
+
+    if (AX == 0 && (a.flags & LF_RECORD)) {
+        // plane spectrum at z = zs: (1/nz) sum_kz p^(kz) e^{+2 pi i kz zs / nz}; partial sums over
+        // this thread's kz, then over the A threads of the line (buf0 is free, see store_k)
+        float2 part = make_float2(0.f, 0.f);
+        if (c.vcol) {
+#pragma unroll
+            for (int k2 = 0; k2 < B; k2++) {
+                const int kz = c.r + A * k2;
+                part = cadd(part, cmul(v[k2], cconj(__ldg(a.tw + ((kz * a.zs) & (L - 1))))));
+            }
+        }
+        c.buf0[c.r * S::TC + c.cl] = part;
+        __syncthreads();
+        if (c.vcol && c.r == 0) {
+            float2 sum = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int rr = 0; rr < A; rr++) sum = cadd(sum, c.buf0[rr * S::TC + c.cl]);
+            a.rec[(size_t)c.b * a.plane_bs + c.col] = cscale(sum, a.s_rec);
+        }
+    }
+}
+
+template <int L>
+LineKernels make_line_kernels() {
+    using S = LS<L>;
+    LineKernels k;
+    k.pass[0] = line_pass_kernel<L, 0>;
+    k.pass[1] = line_pass_kernel<L, 1>;
+    k.pass[2] = line_pass_kernel<L, 2>;
+    k.smem = S::smem;
+    k.tc = S::TC;
+    k.nt = S::NT;
+    return k;
+}
+
+}  // namespace pat

@@ -1,18 +1,20 @@
 // pat_run.cu - launch sequences of A and A^T (Sec. 4.3) on one stream.
 //
 // Forward, T recorded samples (n = 0 is p0 itself):
-//   plane_init                     rho_i = p0/(3c^2), record n = 0, (y,x) FFT of p0
+//   plane_rfft + zfft_fwd          p^0 = F p0 (3D half spectrum); record n = 0 (p0's plane spectrum)
+//   line INIT x, y, z              rho_i^0 = p0 / (3c^2) in each axis's mixed representation
 //   for n = 0 .. T-2:
-//     zpass_grad3  (i k kappa e^{+ik dx/2})     D_i^+ p^n in (z, ky, kx)
-//     plane_vel                                  u_i^{n+1/2}; at n = 0 the half-step start
-//                                                u^{-1/2} = dt/(2 rho0) D^+ p0 is folded into the
-//                                                coefficient as (as/2 - 1) as dt/rho0
-//     zpass_each3  (i k kappa e^{-ik dx/2})     D_i^- u_i
-//     plane_rho_fwd                              rho_i^{n+1}, p^{n+1}, record n+1, FFT of p^{n+1}
-//   sample (C)                                   unless the full plane is recorded
-// Adjoint: C^T, then the same four launches per step in reverse time order with the transposed
-// coefficients (see the adjoint derivation in the oracle: the last step folds the transpose of
-// the initial half step into as (1 - as/2)).
+//     line STEP x, y, z            u_i^{n+1/2}, rho_i^{n+1} and p^{n+1} = c^2 sum F_i rho_i; the z
+//                                  pass records the detection plane's spectrum.  At n = 0 the
+//                                  half-step start u^{-1/2} = dt/(2 rho0) D^+ p0 is folded into the
+//                                  coefficient as (as/2 - 1) dt/rho0.
+//   plane_irfft                    recorded spectra n = 0 .. T-1 -> real planes
+//   sample (C)                     unless the full plane is recorded
+// Adjoint: C^T, plane_rfft of the T injected planes, lambda^{T-1} = their spectrum placed on the
+// plane, then the line passes in reverse time order with the transposed coefficients (the last step
+// folds the transpose of the initial half step into as (1 - as/2)), the image terms
+// a_i^2 q_i / (3 c^2) (line FIN x, y, z), and the inverse 3D transform (zfft_inv + plane_irfft).
+#include "pat_fft.cuh"
 #include "pat_kargs.h"
 
 namespace pat {
@@ -38,15 +40,27 @@ static PlaneKernels plane_kernels_for(int nx, int ny) {
     }
 }
 
+static LineKernels line_kernels_for(int len) {
+    switch (len) {
+        case 8: return line_kernels_l8();
+        case 16: return line_kernels_l16();
+        case 32: return line_kernels_l32();
+        case 64: return line_kernels_l64();
+        case 128: return line_kernels_l128();
+        case 256: return line_kernels_l256();
+        default: return LineKernels{};
+    }
+}
+
 int plane_cluster_size(int nx, int ny) { return plane_kernels_for(nx, ny).cs; }
 
 static const char* g_config_what = "";
 const char* configure_failure() { return g_config_what; }
 
-cudaError_t configure_kernels(const Geom& g, size_t* plane_smem, size_t* z_smem) {
+cudaError_t configure_kernels(const Geom& g) {
     PlaneKernels pk = plane_kernels_for(g.nx, g.ny);
     ZKernels zk = z_kernels_for(g.nz);
-    if (!pk.vel || !zk.grad3) {
+    if (!pk.rfft || !zk.fwd) {
         g_config_what = "no kernel instantiation for this grid shape";
         return cudaErrorInvalidValue;
     }
@@ -58,18 +72,22 @@ cudaError_t configure_kernels(const Geom& g, size_t* plane_smem, size_t* z_smem)
             return _e;                       \
         }                                    \
     } while (0)
-    PAT_CFG(cudaFuncSetAttribute(pk.init, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pk.smem_init), "plane_init smem");
-    PAT_CFG(cudaFuncSetAttribute(pk.vel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pk.smem3), "plane_vel smem");
-    PAT_CFG(cudaFuncSetAttribute(pk.rho_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pk.smem3), "plane_rho_fwd smem");
-    PAT_CFG(cudaFuncSetAttribute(pk.rho_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pk.smem3), "plane_rho_adj smem");
-    PAT_CFG(cudaFuncSetAttribute(zk.grad3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zk.smem), "zpass_grad3 smem");
-    PAT_CFG(cudaFuncSetAttribute(zk.each3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zk.smem), "zpass_each3 smem");
-    PAT_CFG(cudaFuncSetAttribute(zk.sum3, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zk.smem), "zpass_sum3 smem");
+    PAT_CFG(cudaFuncSetAttribute(pk.rfft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pk.smem), "plane_rfft smem");
+    PAT_CFG(cudaFuncSetAttribute(pk.irfft, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pk.smem), "plane_irfft smem");
+    PAT_CFG(cudaFuncSetAttribute(zk.fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zk.smem), "zfft_fwd smem");
+    PAT_CFG(cudaFuncSetAttribute(zk.inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)zk.smem), "zfft_inv smem");
+    for (int ax = 0; ax < 3; ax++) {
+        LineKernels lk = line_kernels_for(g.len[ax]);
+        if (!lk.pass[ax]) {
+            g_config_what = "no line kernel for this axis length";
+            return cudaErrorInvalidValue;
+        }
+        PAT_CFG(cudaFuncSetAttribute(lk.pass[ax], cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lk.smem),
+                "line pass smem");
+    }
     PAT_CFG(configure_sampling(g), "sampling smem");
 #undef PAT_CFG
     g_config_what = "";
-    if (plane_smem) *plane_smem = pk.smem3;
-    if (z_smem) *z_smem = zk.smem;
     return cudaSuccess;
 }
 
@@ -88,22 +106,29 @@ static cudaError_t timed(Profiler* prof, int cls, cudaStream_t st, F&& launch) {
     return cudaSuccess;
 }
 
-// Time-loop kernels are launched with programmatic stream serialisation (they call pdl_wait()
-// before touching memory), so each one is scheduled while its predecessor drains.
-static cudaError_t launch_plane(PlaneKernel k, size_t smem, int cs, const PlaneArgs& a, cudaStream_t st) {
-    const Geom& g = a.g;
+// Kernels are launched with programmatic stream serialisation (they call pdl_wait() before touching
+// memory), so each one is scheduled while its predecessor drains.
+static cudaLaunchAttribute pdl_attr() {
+    cudaLaunchAttribute at;
+    at.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at.val.programmaticStreamSerializationAllowed = 1;
+    return at;
+}
+
+static cudaError_t launch_plane(PlaneKernel k, const PlaneKernels& pk, int nplanes, const PlaneArgs& a,
+                                cudaStream_t st) {
+    if (nplanes <= 0) return cudaSuccess;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(cs, g.nz, g.B);
+    cfg.gridDim = dim3(pk.cs, nplanes, a.g.B);
     cfg.blockDim = dim3(kPlaneThreads, 1, 1);
-    cfg.dynamicSmemBytes = smem;
+    cfg.dynamicSmemBytes = pk.smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = cs;
+    attr[0].val.clusterDim.x = pk.cs;
     attr[0].val.clusterDim.y = 1;
     attr[0].val.clusterDim.z = 1;
-    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[1].val.programmaticStreamSerializationAllowed = 1;
+    attr[1] = pdl_attr();
     cfg.attrs = attr;
     cfg.numAttrs = 2;
     return cudaLaunchKernelEx(&cfg, k, a);
@@ -112,88 +137,152 @@ static cudaError_t launch_plane(PlaneKernel k, size_t smem, int cs, const PlaneA
 static cudaError_t launch_z(ZKernel k, const ZKernels& zk, const ZArgs& a, cudaStream_t st) {
     const int ncols = a.g.ny * a.g.nxh;
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3((ncols + zk.tc - 1) / zk.tc, a.g.B, k == zk.each3 ? 3 : 1);
+    cfg.gridDim = dim3((ncols + zk.tc - 1) / zk.tc, a.g.B, 1);
     cfg.blockDim = dim3(zk.nt, 1, 1);
     cfg.dynamicSmemBytes = zk.smem;
     cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchAttribute attr[1] = {pdl_attr()};
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     return cudaLaunchKernelEx(&cfg, k, a);
 }
 
-static PlaneArgs plane_base(const Geom& g, const DeviceTables& t, const Workspace& w) {
-    PlaneArgs a = {};
+static cudaError_t launch_line(int ax, const LineArgs& a, cudaStream_t st) {
+    const LineKernels lk = line_kernels_for(a.g.len[ax]);
+    if (!lk.pass[ax]) return cudaErrorInvalidValue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((a.ncols + lk.tc - 1) / lk.tc, a.g.B, 1);
+    cfg.blockDim = dim3(lk.nt, 1, 1);
+    cfg.dynamicSmemBytes = lk.smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1] = {pdl_attr()};
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, lk.pass[ax], a);
+}
+
+static const int kLineClass[3] = {KC_LINE_Z, KC_LINE_Y, KC_LINE_X};
+static const int kPassOrder[3] = {AX, AY, AZ};  // x writes the new spectrum, y and z add to it
+
+// spec[b][kz][c] = S[b][c] exp(-2 pi i kz zs / nz): the 3D spectrum of a plane source at z = zs
+__global__ void spread_plane_kernel(Geom g, const float2* __restrict__ tw_z, const float2* __restrict__ S,
+                                    long long s_bs, float2* __restrict__ spec) {
+    const long long nplane = g.nplane;
+    const long long total = (long long)g.B * g.nz * nplane;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long c = i % nplane;
+        const long long kz = (i / nplane) % g.nz;
+        const long long b = i / (nplane * g.nz);
+        const float2 w = tw_z[(kz * g.sensor_z) & (g.nz - 1)];
+        spec[i] = cmul(S[b * s_bs + c], w);
+    }
+}
+
+cudaError_t launch_spread_plane(const Geom& g, const float2* tw_z, const float2* S, long long s_bs,
+                                float2* spec, cudaStream_t st) {
+    const long long total = (long long)g.B * g.nz * g.nplane;
+    const int nt = 256;
+    const long long nb = (total + nt - 1) / nt;
+    spread_plane_kernel<<<(unsigned)(nb < 4096 ? nb : 4096), nt, 0, st>>>(g, tw_z, S, s_bs, spec);
+    return cudaGetLastError();
+}
+
+static LineArgs line_base(const Geom& g, const DeviceTables& t, const Workspace& w, int ax) {
+    LineArgs a = {};
     a.g = g;
-    a.tw_x = t.tw[AX];
-    a.tw_y = t.tw[AY];
-    for (int i = 0; i < 3; i++) a.spec[i] = w.spec[i];
+    a.ncols = g.ncols[ax];
+    a.tw = t.tw[ax];
+    a.st1 = w.ms[ax][0];
+    a.st2 = w.ms[ax][1];
+    a.kap = t.kappa[ax];
+    a.zs = g.sensor_z;
+    a.plane_bs = (long long)g.T * g.nplane;
+    a.s_rec = 1.0f / (float)g.nz;
     return a;
 }
 
-static ZArgs z_base(const Geom& g, const DeviceTables& t, const Workspace& w, bool plus) {
-    ZArgs a = {};
-    a.g = g;
-    a.tw_z = t.tw[AZ];
-    for (int i = 0; i < 3; i++) {
-        a.spec[i] = w.spec[i];
-        a.dt[i] = plus ? t.dplus[i] : t.dminus[i];
-    }
-    a.kappaN = t.kappaN;
-    return a;
-}
-
-static void set_tables(PlaneArgs& a, const DeviceTables& t, int c1, int c2, int c3) {
-    for (int i = 0; i < 3; i++) {
-        a.A1[i] = t.coef[c1][i];
-        a.A2[i] = t.coef[c2][i];
-        a.A3[i] = t.coef[c3][i];
-    }
+static void set_coef(const float** dst, const DeviceTables& t, int ax, int c0, int c1, int c2) {
+    dst[0] = t.coef[c0][ax];
+    dst[1] = t.coef[c1][ax];
+    dst[2] = t.coef[c2][ax];
 }
 
 cudaError_t run_forward(const Geom& g, const DeviceTables& t, const Workspace& w, const Scalars& s,
                         int kind, int m, const float* p0, float* f, cudaStream_t st, Profiler* prof) {
     const PlaneKernels pk = plane_kernels_for(g.nx, g.ny);
     const ZKernels zk = z_kernels_for(g.nz);
-    if (!pk.vel || !zk.grad3) return cudaErrorInvalidValue;
+    if (!pk.rfft || !zk.fwd) return cudaErrorInvalidValue;
     float* rec = (kind == PAT_SAMPLE_FULL) ? f : w.rec;
-    const float c2 = (float)(s.c * s.c);
+    const long long M = g.m_plane;
 
-    PlaneArgs pi = plane_base(g, t, w);
-    pi.flags = (g.T == 1) ? PF_NO_FWD : 0;
-    pi.in_real = p0;
-    for (int i = 0; i < 3; i++) pi.st[i] = w.st[3 + i];
-    pi.s1 = (float)(1.0 / (3.0 * s.c * s.c));
-    pi.rec = rec;
-    pi.n_rec = 0;
-    PAT_TRY(timed(prof, KC_PLANE_INIT, st, [&] { return launch_plane(pk.init, pk.smem_init, pk.cs, pi, st); }));
+    // p^0 = F p0; the record's plane 0 is p0's detection plane, taken through its (kx, ky) spectrum
+    // like every other plane (the real series may share memory with the loop state)
+    PlaneArgs pa = {};
+    pa.g = g;
+    pa.tw_x = t.tw[AX];
+    pa.tw_y = t.tw[AY];
+    pa.in_real = p0;
+    pa.bs_real = g.nreal;
+    pa.spec_out = w.ph[0];
+    pa.bs_spec = g.nspec;
+    PAT_TRY(timed(prof, KC_PLANE_FFT, st, [&] { return launch_plane(pk.rfft, pk, g.nz, pa, st); }));
+    PAT_TRY(cudaMemcpy2DAsync(w.rk, (size_t)g.T * g.nplane * sizeof(float2),
+                              w.ph[0] + (size_t)g.sensor_z * g.nplane, (size_t)g.nspec * sizeof(float2),
+                              (size_t)g.nplane * sizeof(float2), (size_t)g.B, cudaMemcpyDeviceToDevice, st));
+    if (g.T > 1) {
+        ZArgs za = {};
+        za.g = g;
+        za.tw_z = t.tw[AZ];
+        za.spec = w.ph[0];
+        za.scale = 1.0f;
+        PAT_TRY(timed(prof, KC_Z_FFT, st, [&] { return launch_z(zk.fwd, zk, za, st); }));
 
-    const ZArgs zg = z_base(g, t, w, true);
-    const ZArgs zd = z_base(g, t, w, false);
-    PlaneArgs pv = plane_base(g, t, w);
-    for (int i = 0; i < 3; i++) pv.st[i] = w.st[i];
-    PlaneArgs pr = plane_base(g, t, w);
-    for (int i = 0; i < 3; i++) pr.st[i] = w.st[3 + i];
-    set_tables(pr, t, CT_A2, CT_DF_D, CT_ONE);
-    pr.c2 = c2;
-    pr.rec = rec;
-    for (int n = 0; n + 1 < g.T; n++) {
-        PAT_TRY(timed(prof, KC_Z_ONE_TO_THREE, st, [&] { return launch_z(zk.grad3, zk, zg, st); }));
-        if (n == 0) {
-            set_tables(pv, t, CT_AS2, CT_VF0_G, CT_ONE);
-            pv.flags = PF_NO_OLD;
-        } else {
-            set_tables(pv, t, CT_AS2, CT_VF_G, CT_ONE);
-            pv.flags = 0;
+        const double c2 = s.c * s.c;
+        for (int ax : kPassOrder) {
+            LineArgs li = line_base(g, t, w, ax);
+            li.mode = LM_INIT;
+            li.in = w.ph[0];
+            li.s_pre = (float)(1.0 / (3.0 * c2 * g.len[ax]));
+            PAT_TRY(timed(prof, kLineClass[ax], st, [&] { return launch_line(ax, li, st); }));
         }
-        PAT_TRY(timed(prof, KC_PLANE_VEL, st, [&] { return launch_plane(pk.vel, pk.smem3, pk.cs, pv, st); }));
-        PAT_TRY(timed(prof, KC_Z_THREE_TO_THREE, st, [&] { return launch_z(zk.each3, zk, zd, st); }));
-        pr.n_rec = n + 1;
-        pr.flags = (n + 2 == g.T) ? PF_NO_FWD : 0;
-        PAT_TRY(timed(prof, KC_PLANE_RHO_FWD, st, [&] { return launch_plane(pk.rho_fwd, pk.smem3, pk.cs, pr, st); }));
+        LineArgs la[3];
+        for (int ax = 0; ax < 3; ax++) {
+            la[ax] = line_base(g, t, w, ax);
+            la[ax].mode = LM_STEP;
+            la[ax].dpre = t.dplus[ax];
+            la[ax].dmid = t.dminus[ax];
+            la[ax].dpost = nullptr;
+            la[ax].s_pre = (float)(1.0 / g.len[ax]);
+            la[ax].s_mid = (float)(1.0 / g.len[ax]);
+            la[ax].s_post = (float)c2;
+            set_coef(la[ax].c2, t, ax, CT_A2, CT_DF_D, CT_ONE);
+        }
+        for (int n = 0; n + 1 < g.T; n++) {
+            float2* cur = w.ph[n & 1];
+            float2* nxt = w.ph[(n + 1) & 1];
+            for (int ax : kPassOrder) {
+                LineArgs& a = la[ax];
+                a.in = cur;
+                a.out = nxt;
+                set_coef(a.c1, t, ax, CT_AS2, (n == 0) ? CT_VF0_G : CT_VF_G, CT_ONE);
+                a.flags = (n == 0 ? LF_NO_OLD1 : 0) | (ax == AX ? 0 : LF_ACCUM) | (ax == AZ ? LF_RECORD : 0);
+                a.rec = w.rk + (size_t)(n + 1) * g.nplane;
+                PAT_TRY(timed(prof, kLineClass[ax], st, [&] { return launch_line(ax, a, st); }));
+            }
+        }
     }
+    // recorded spectra -> real planes
+    PlaneArgs pr = {};
+    pr.g = g;
+    pr.tw_x = t.tw[AX];
+    pr.tw_y = t.tw[AY];
+    pr.spec_in = w.rk;
+    pr.bs_spec = (long long)g.T * g.nplane;
+    pr.out_real = rec;
+    pr.bs_real = (long long)g.T * M;
+    pr.scale = (float)(1.0 / ((double)g.nx * g.ny));
+    PAT_TRY(timed(prof, KC_PLANE_FFT, st, [&] { return launch_plane(pk.irfft, pk, g.T, pr, st); }));
     if (kind != PAT_SAMPLE_FULL)
         PAT_TRY(timed(prof, KC_SAMPLE, st, [&] { return run_sample(g, w, kind, m, rec, f, g.T, st); }));
     return cudaSuccess;
@@ -203,41 +292,80 @@ cudaError_t run_adjoint(const Geom& g, const DeviceTables& t, const Workspace& w
                         int kind, int m, const float* f, float* p, cudaStream_t st, Profiler* prof) {
     const PlaneKernels pk = plane_kernels_for(g.nx, g.ny);
     const ZKernels zk = z_kernels_for(g.nz);
-    if (!pk.vel || !zk.grad3) return cudaErrorInvalidValue;
+    if (!pk.rfft || !zk.fwd) return cudaErrorInvalidValue;
     const float* inj = f;
     if (kind != PAT_SAMPLE_FULL) {
         PAT_TRY(timed(prof, KC_SAMPLE, st, [&] { return run_sample_adjoint(g, w, kind, m, f, w.rec, g.T, st); }));
         inj = w.rec;
     }
     if (g.T == 1) return run_inject_only(g, inj, p, st);
-    const float c2 = (float)(s.c * s.c);
-    PlaneArgs pq = plane_base(g, t, w);
-    for (int i = 0; i < 3; i++) pq.st[i] = w.st[3 + i];
-    set_tables(pq, t, CT_A2, CT_ONE, CT_A);
-    pq.c2 = c2;
-    pq.s0 = (float)(s.dt / s.rho0);
-    pq.s1 = (float)(1.0 / (3.0 * s.c * s.c));
-    pq.inj = inj;
-    pq.out_real = p;
-    // q_i^{T-1} = c^2 (injected plane T-1); transform a_i q_i
-    pq.flags = PF_NO_OLD;
-    pq.n_rec = g.T - 1;
-    PAT_TRY(timed(prof, KC_PLANE_RHO_ADJ, st, [&] { return launch_plane(pk.rho_adj, pk.smem3, pk.cs, pq, st); }));
+    const long long M = g.m_plane;
 
-    const ZArgs zg = z_base(g, t, w, true);
-    const ZArgs zd = z_base(g, t, w, false);
-    PlaneArgs pv = plane_base(g, t, w);
-    for (int i = 0; i < 3; i++) pv.st[i] = w.st[i];
-    for (int n = g.T - 2; n >= 0; n--) {
-        PAT_TRY(timed(prof, KC_Z_THREE_TO_THREE, st, [&] { return launch_z(zk.each3, zk, zg, st); }));
-        set_tables(pv, t, CT_AS2, CT_VA_G, (n == 0) ? CT_VA0_OUT : CT_AS);
-        pv.flags = (n + 2 == g.T) ? PF_NO_OLD : 0;
-        PAT_TRY(timed(prof, KC_PLANE_VEL, st, [&] { return launch_plane(pk.vel, pk.smem3, pk.cs, pv, st); }));
-        PAT_TRY(timed(prof, KC_Z_THREE_TO_ONE, st, [&] { return launch_z(zk.sum3, zk, zd, st); }));
-        pq.flags = PF_HAVE_LAMBDA | ((n == 0) ? PF_FINAL : 0);
-        pq.n_rec = n;
-        PAT_TRY(timed(prof, KC_PLANE_RHO_ADJ, st, [&] { return launch_plane(pk.rho_adj, pk.smem3, pk.cs, pq, st); }));
+    // spectra of the T injected planes; lambda^{T-1} = the last one placed on the detection plane
+    PlaneArgs pa = {};
+    pa.g = g;
+    pa.tw_x = t.tw[AX];
+    pa.tw_y = t.tw[AY];
+    pa.in_real = inj;
+    pa.bs_real = (long long)g.T * M;
+    pa.spec_out = w.rk;
+    pa.bs_spec = (long long)g.T * g.nplane;
+    PAT_TRY(timed(prof, KC_PLANE_FFT, st, [&] { return launch_plane(pk.rfft, pk, g.T, pa, st); }));
+    const long long s_bs = (long long)g.T * g.nplane;
+    PAT_TRY(launch_spread_plane(g, t.tw[AZ], w.rk + (size_t)(g.T - 1) * g.nplane, s_bs, w.ph[0], st));
+
+    LineArgs la[3];
+    for (int ax = 0; ax < 3; ax++) {
+        la[ax] = line_base(g, t, w, ax);
+        la[ax].mode = LM_STEP;
+        la[ax].dpre = nullptr;
+        la[ax].dmid = t.dplus[ax];
+        la[ax].dpost = t.dminus[ax];
+        la[ax].s_pre = (float)(1.0 / g.len[ax]);
+        la[ax].s_mid = (float)(1.0 / g.len[ax]);
+        la[ax].s_post = (float)(s.dt / s.rho0);
+        set_coef(la[ax].c1, t, ax, CT_A2, CT_C2, CT_A);
     }
+    int cur = 0;
+    for (int n = g.T - 2; n >= 0; n--) {
+        for (int ax : kPassOrder) {
+            LineArgs& a = la[ax];
+            a.in = w.ph[cur];
+            a.out = w.ph[cur ^ 1];
+            set_coef(a.c2, t, ax, CT_AS2, CT_VA_G, (n == 0) ? CT_VA0_OUT : CT_AS);
+            a.flags = (n == g.T - 2 ? (LF_NO_OLD1 | LF_NO_OLD2) : 0) | (ax == AX ? 0 : LF_ACCUM) |
+                      (ax == AZ ? LF_INJECT : 0);
+            a.inj = w.rk + (size_t)n * g.nplane;
+            PAT_TRY(timed(prof, kLineClass[ax], st, [&] { return launch_line(ax, a, st); }));
+        }
+        cur ^= 1;
+    }
+    // image terms a_i^2 q_i / (3 c^2) of rho_i^0 = p0 / (3 c^2)
+    for (int ax : kPassOrder) {
+        LineArgs a = line_base(g, t, w, ax);
+        a.mode = LM_FIN;
+        a.out = w.ph[cur];
+        a.c1[0] = t.coef[CT_FIN][ax];
+        a.flags = LF_ACCUM;
+        PAT_TRY(timed(prof, kLineClass[ax], st, [&] { return launch_line(ax, a, st); }));
+    }
+    // p = F^-1 lambda^0
+    ZArgs za = {};
+    za.g = g;
+    za.tw_z = t.tw[AZ];
+    za.spec = w.ph[cur];
+    za.scale = (float)(1.0 / g.nz);
+    PAT_TRY(timed(prof, KC_Z_FFT, st, [&] { return launch_z(zk.inv, zk, za, st); }));
+    PlaneArgs pr = {};
+    pr.g = g;
+    pr.tw_x = t.tw[AX];
+    pr.tw_y = t.tw[AY];
+    pr.spec_in = w.ph[cur];
+    pr.bs_spec = g.nspec;
+    pr.out_real = p;
+    pr.bs_real = g.nreal;
+    pr.scale = (float)(1.0 / ((double)g.nx * g.ny));
+    PAT_TRY(timed(prof, KC_PLANE_FFT, st, [&] { return launch_plane(pk.irfft, pk, g.nz, pr, st); }));
     return cudaSuccess;
 }
 

@@ -26,7 +26,9 @@
 // k-space layout thread r < A holds X[r + A k2] (k2 < B), in the spatial layout thread r < B holds
 // x[r + B k2] (k2 < A); each transform is one exchange through shared memory laid out [row][line]
 // with the line index fastest.  Two exchange buffers alternate, so every transform costs one
-// barrier.
+// barrier.  The old values of both states, and of the spectrum a y or z pass adds to, are copied to
+// shared memory with cp.async as soon as the kernel starts, so their latency overlaps the first
+// transforms instead of stalling each update.
 //
 // Spectrum access per axis (3D half spectrum [kz][kx][ky], kx <= nx/2):
 //   z lines (kx, ky): column access, stride nxh*ny
@@ -45,11 +47,13 @@ template <int L>
 struct LS {
     static constexpr int A = Split<L>::A;  // values per thread, spatial layout
     static constexpr int B = Split<L>::B;  // values per thread, k-space layout
-    static constexpr int TC = (L >= 128) ? 16 : 32;
+    // lines per CTA: about 1024 line points per CTA (8 KB tiles), at least 8 lines (64-byte rows)
+    static constexpr int TC = (1024 / L > 32) ? 32 : (1024 / L < 8 ? 8 : 1024 / L);
     static constexpr int NT = A * TC;
     static constexpr int PITCH = L + 1;     // staging row pitch for y lines
     static constexpr int BUF = L * TC + TC; // one exchange buffer (float2), also holds TC staged rows
-    static constexpr size_t smem = 2 * (size_t)BUF * sizeof(float2);
+    static constexpr int TILE = L * TC;     // one prefetched tile (float2)
+    static constexpr size_t smem = (2 * (size_t)BUF + 3 * (size_t)TILE) * sizeof(float2);
     static constexpr int MINB = (NT >= 256) ? 2 : 4;
 };
 
@@ -60,6 +64,9 @@ struct LineCtx {
     const LineArgs& a;
     float2* buf0;
     float2* buf1;
+    float2* pf1;    // prefetched old state 1, [j][line]
+    float2* pf2;    // prefetched old state 2
+    float2* pfo;    // prefetched old output: z lines [kz][line], y lines the contiguous row block
     int cl, r, col, col0, b;
     bool vcol;
     size_t sbase;   // state element of this line at position 0
@@ -70,6 +77,9 @@ struct LineCtx {
     __device__ LineCtx(const LineArgs& args, float2* smem) : a(args) {
         buf0 = smem;
         buf1 = smem + S::BUF;
+        pf1 = smem + 2 * S::BUF;
+        pf2 = pf1 + S::TILE;
+        pfo = pf2 + S::TILE;
         const int tid = threadIdx.x;
         cl = tid % TC;
         r = tid / TC;
@@ -168,9 +178,9 @@ struct LineCtx {
             if (vcol) {
 #pragma unroll
                 for (int k2 = 0; k2 < B; k2++) {
-                    float2* p = out + pbase + (size_t)(r + A * k2) * a.ncols + col;
-                    if (accum) v[k2] = cadd(*p, v[k2]);
-                    *p = v[k2];
+                    const int j = r + A * k2;
+                    if (accum) v[k2] = cadd(pfo[j * TC + cl], v[k2]);
+                    out[pbase + (size_t)j * a.ncols + col] = v[k2];
                 }
             }
         } else if (AX == 1) {
@@ -188,7 +198,7 @@ struct LineCtx {
                 const float2* s = buf0 + row * S::PITCH + pt;
                 float4 w = make_float4(s[0].x, s[0].y, s[1].x, s[1].y);
                 if (accum) {
-                    const float4 o = blk[e];
+                    const float4 o = reinterpret_cast<const float4*>(pfo)[e];
                     w.x += o.x; w.y += o.y; w.z += o.z; w.w += o.w;
                 }
                 blk[e] = w;
@@ -216,27 +226,62 @@ struct LineCtx {
 
     // ---- pointwise state update in the spatial layout: s = c[0] s + c[1] x (no old: s = c[1] x),
     // x = c[2] s
+    // (old values from the prefetched tile pf)
     __device__ __forceinline__ void update(float2* __restrict__ st, const float* const* c, bool no_old,
-                                           float2* x) const {
+                                           const float2* pf, float2* x) const {
         if (vcol && r < B) {
-            float2 o[A];
-            if (!no_old) {
-#pragma unroll
-                for (int k2 = 0; k2 < A; k2++) o[k2] = st[sbase + (size_t)(r + B * k2) * a.ncols];
-            }
 #pragma unroll
             for (int k2 = 0; k2 < A; k2++) {
                 const int j = r + B * k2;
                 float2 nv = cscale(x[k2], __ldg(c[1] + j));
                 if (!no_old) {
                     const float d = __ldg(c[0] + j);
-                    nv.x = fmaf(d, o[k2].x, nv.x);
-                    nv.y = fmaf(d, o[k2].y, nv.y);
+                    const float2 o = pf[j * TC + cl];
+                    nv.x = fmaf(d, o.x, nv.x);
+                    nv.y = fmaf(d, o.y, nv.y);
                 }
                 st[sbase + (size_t)j * a.ncols] = nv;
                 x[k2] = cscale(nv, __ldg(c[2] + j));
             }
         }
+    }
+
+    // issue the cp.async copies of the old states and the old output (three commit groups, in that
+    // order; every thread commits all three, empty or not)
+    __device__ __forceinline__ void prefetch(bool old1, bool old2, bool accum) const {
+        if (old1 && vcol && r < B) {
+#pragma unroll
+            for (int k2 = 0; k2 < A; k2++) {
+                const int j = r + B * k2;
+                cp_async8(pf1 + j * TC + cl, a.st1 + sbase + (size_t)j * a.ncols);
+            }
+        }
+        cp_async_commit();
+        if (old2 && vcol && r < B) {
+#pragma unroll
+            for (int k2 = 0; k2 < A; k2++) {
+                const int j = r + B * k2;
+                cp_async8(pf2 + j * TC + cl, a.st2 + sbase + (size_t)j * a.ncols);
+            }
+        }
+        cp_async_commit();
+        if (accum) {
+            if (AX == 0) {
+                if (vcol) {
+#pragma unroll
+                    for (int k2 = 0; k2 < B; k2++) {
+                        const int j = r + A * k2;
+                        cp_async8(pfo + j * TC + cl, a.out + pbase + (size_t)j * a.ncols + col);
+                    }
+                }
+            } else if (AX == 1) {
+                const int nrows = min(TC, a.ncols - col0);
+                const float4* blk = reinterpret_cast<const float4*>(a.out + pbase + (size_t)col0 * L);
+                for (int e = threadIdx.x; e < nrows * (L / 2); e += S::NT)
+                    cp_async16(reinterpret_cast<float4*>(pfo) + e, blk + e);
+            }
+        }
+        cp_async_commit();
     }
 
     // k-space factor D[j] kappa s (D == NULL: s)
@@ -266,6 +311,7 @@ __global__ void __launch_bounds__(LS<L>::NT, LS<L>::MINB) line_pass_kernel(LineA
 
     if (a.mode == LM_FIN) {
         // adjoint image term: out += F_i (c1[0] st1)
+        c.prefetch(false, false, true);
         if (c.vcol && c.r < B) {
 #pragma unroll
             for (int k2 = 0; k2 < A; k2++) {
@@ -274,10 +320,13 @@ __global__ void __launch_bounds__(LS<L>::NT, LS<L>::MINB) line_pass_kernel(LineA
             }
         }
         c.fwd(x, v, c.buf1);
+        cp_async_wait<0>();
         c.store_k(a.out, v, true);
         return;
     }
 
+    if (a.mode == LM_STEP)
+        c.prefetch((a.flags & LF_NO_OLD1) == 0, (a.flags & LF_NO_OLD2) == 0, accum);
     c.load_k(a.in, v);
     if (a.mode == LM_INIT) {
         // forward start: st2 = F_i^-1[p^] s_pre  (rho_i^0 = p0 / (3 c^2))
@@ -297,12 +346,15 @@ __global__ void __launch_bounds__(LS<L>::NT, LS<L>::MINB) line_pass_kernel(LineA
 
     c.factor(v, a.dpre, kap, a.s_pre);
     c.inv(v, x, c.buf0);
-    c.update(a.st1, a.c1, (a.flags & LF_NO_OLD1) != 0, x);
+    cp_async_wait<2>();
+    c.update(a.st1, a.c1, (a.flags & LF_NO_OLD1) != 0, c.pf1, x);
     c.fwd(x, v, c.buf1);
     c.factor(v, a.dmid, kap, a.s_mid);
     c.inv(v, x, c.buf0);
-    c.update(a.st2, a.c2, (a.flags & LF_NO_OLD2) != 0, x);
+    cp_async_wait<1>();
+    c.update(a.st2, a.c2, (a.flags & LF_NO_OLD2) != 0, c.pf2, x);
     c.fwd(x, v, c.buf1);
+    cp_async_wait<0>();
     c.factor(v, a.dpost, kap, a.s_post);
 
     if (AX == 0 && (a.flags & LF_INJECT) && c.vcol) {

@@ -26,9 +26,15 @@
 // k-space layout thread r < A holds X[r + A k2] (k2 < B), in the spatial layout thread r < B holds
 // x[r + B k2] (k2 < A); each transform is one exchange through shared memory laid out [row][line]
 // with the line index fastest.  Two exchange buffers alternate, so every transform costs one
-// barrier.  The old values of both states, and of the spectrum a y or z pass adds to, are copied to
-// shared memory with cp.async as soon as the kernel starts, so their latency overlaps the first
-// transforms instead of stalling each update.
+// barrier.  The old values of both states are copied to shared memory with cp.async as soon as the
+// kernel starts, so their latency overlaps the first transforms instead of stalling each update.
+//
+// Launch overlap.  The y and z passes of a step read only the previous step's spectrum and their own
+// states until they add to the new spectrum, so they are launched as programmatic dependents that
+// start at once and wait for their predecessor (griddepcontrol.wait) only before that last stage
+// (LF_LATE_WAIT).  Everything they read before the wait was written by kernels that had completed
+// before the x pass of the step passed its own wait, and is read through L2 (ld.cg, cp.async.cg).
+// No kernel waits on a grid whose CTAs have not all started, so the overlap cannot deadlock.
 //
 // Spectrum access per axis (3D half spectrum [kz][kx][ky], kx <= nx/2):
 //   z lines (kx, ky): column access, stride nxh*ny
@@ -52,8 +58,8 @@ struct LS {
     static constexpr int NT = A * TC;
     static constexpr int PITCH = L + 1;     // staging row pitch for y lines
     static constexpr int BUF = L * TC + TC; // one exchange buffer (float2), also holds TC staged rows
-    static constexpr int TILE = L * TC;     // one prefetched tile (float2)
-    static constexpr size_t smem = (2 * (size_t)BUF + 3 * (size_t)TILE) * sizeof(float2);
+    static constexpr int TILE = L * TC;     // one prefetched state tile (float2)
+    static constexpr size_t smem = (2 * (size_t)BUF + 2 * (size_t)TILE) * sizeof(float2);
     static constexpr int MINB = (NT >= 256) ? 2 : 4;
 };
 
@@ -66,7 +72,6 @@ struct LineCtx {
     float2* buf1;
     float2* pf1;    // prefetched old state 1, [j][line]
     float2* pf2;    // prefetched old state 2
-    float2* pfo;    // prefetched old output: z lines [kz][line], y lines the contiguous row block
     int cl, r, col, col0, b;
     bool vcol;
     size_t sbase;   // state element of this line at position 0
@@ -79,7 +84,6 @@ struct LineCtx {
         buf1 = smem + S::BUF;
         pf1 = smem + 2 * S::BUF;
         pf2 = pf1 + S::TILE;
-        pfo = pf2 + S::TILE;
         const int tid = threadIdx.x;
         cl = tid % TC;
         r = tid / TC;
@@ -139,13 +143,13 @@ struct LineCtx {
         if (AX == 0) {
             if (vcol) {
 #pragma unroll
-                for (int k2 = 0; k2 < B; k2++) v[k2] = in[pbase + (size_t)(r + A * k2) * a.ncols + col];
+                for (int k2 = 0; k2 < B; k2++) v[k2] = __ldcg(in + pbase + (size_t)(r + A * k2) * a.ncols + col);
             }
         } else if (AX == 1) {
             const int nrows = min(TC, a.ncols - col0);
             const float4* blk = reinterpret_cast<const float4*>(in + pbase + (size_t)col0 * L);
             for (int e = threadIdx.x; e < nrows * (L / 2); e += S::NT) {
-                const float4 w = blk[e];
+                const float4 w = __ldcg(blk + e);
                 const int row = (2 * e) / L, pt = (2 * e) % L;
                 float2* d = buf1 + row * S::PITCH + pt;
                 d[0] = make_float2(w.x, w.y);
@@ -178,9 +182,9 @@ struct LineCtx {
             if (vcol) {
 #pragma unroll
                 for (int k2 = 0; k2 < B; k2++) {
-                    const int j = r + A * k2;
-                    if (accum) v[k2] = cadd(pfo[j * TC + cl], v[k2]);
-                    out[pbase + (size_t)j * a.ncols + col] = v[k2];
+                    float2* p = out + pbase + (size_t)(r + A * k2) * a.ncols + col;
+                    if (accum) v[k2] = cadd(*p, v[k2]);
+                    *p = v[k2];
                 }
             }
         } else if (AX == 1) {
@@ -198,7 +202,7 @@ struct LineCtx {
                 const float2* s = buf0 + row * S::PITCH + pt;
                 float4 w = make_float4(s[0].x, s[0].y, s[1].x, s[1].y);
                 if (accum) {
-                    const float4 o = reinterpret_cast<const float4*>(pfo)[e];
+                    const float4 o = blk[e];
                     w.x += o.x; w.y += o.y; w.z += o.z; w.w += o.w;
                 }
                 blk[e] = w;
@@ -246,39 +250,24 @@ struct LineCtx {
         }
     }
 
-    // issue the cp.async copies of the old states and the old output (three commit groups, in that
-    // order; every thread commits all three, empty or not)
-    __device__ __forceinline__ void prefetch(bool old1, bool old2, bool accum) const {
-        if (old1 && vcol && r < B) {
-#pragma unroll
-            for (int k2 = 0; k2 < A; k2++) {
-                const int j = r + B * k2;
-                cp_async8(pf1 + j * TC + cl, a.st1 + sbase + (size_t)j * a.ncols);
+    // issue the cp.async copies of the old states (two commit groups, state 1 then state 2; every
+    // thread commits both).  16-byte copies of column pairs (ncols and the tile start are even), so a
+    // thread's copies are not the values it later reads: consumers wait, then pass a barrier.
+    __device__ __forceinline__ void prefetch(bool old1, bool old2) const {
+        constexpr int NCH = L * (TC / 2);  // 16-byte chunks per tile
+        const int ncol2 = min(TC, a.ncols - col0) / 2;
+        const size_t base = (size_t)b * L * a.ncols + col0;
+        if (old1) {
+            for (int q = threadIdx.x; q < NCH; q += S::NT) {
+                const int j = q / (TC / 2), cc = q % (TC / 2);
+                if (cc < ncol2) cp_async16(pf1 + j * TC + 2 * cc, a.st1 + base + (size_t)j * a.ncols + 2 * cc);
             }
         }
         cp_async_commit();
-        if (old2 && vcol && r < B) {
-#pragma unroll
-            for (int k2 = 0; k2 < A; k2++) {
-                const int j = r + B * k2;
-                cp_async8(pf2 + j * TC + cl, a.st2 + sbase + (size_t)j * a.ncols);
-            }
-        }
-        cp_async_commit();
-        if (accum) {
-            if (AX == 0) {
-                if (vcol) {
-#pragma unroll
-                    for (int k2 = 0; k2 < B; k2++) {
-                        const int j = r + A * k2;
-                        cp_async8(pfo + j * TC + cl, a.out + pbase + (size_t)j * a.ncols + col);
-                    }
-                }
-            } else if (AX == 1) {
-                const int nrows = min(TC, a.ncols - col0);
-                const float4* blk = reinterpret_cast<const float4*>(a.out + pbase + (size_t)col0 * L);
-                for (int e = threadIdx.x; e < nrows * (L / 2); e += S::NT)
-                    cp_async16(reinterpret_cast<float4*>(pfo) + e, blk + e);
+        if (old2) {
+            for (int q = threadIdx.x; q < NCH; q += S::NT) {
+                const int j = q / (TC / 2), cc = q % (TC / 2);
+                if (cc < ncol2) cp_async16(pf2 + j * TC + 2 * cc, a.st2 + base + (size_t)j * a.ncols + 2 * cc);
             }
         }
         cp_async_commit();
@@ -303,7 +292,8 @@ __global__ void __launch_bounds__(LS<L>::NT, LS<L>::MINB) line_pass_kernel(LineA
     constexpr int A = S::A, B = S::B;
     extern __shared__ float4 smem_raw[];
     LineCtx<L, AX> c(a, reinterpret_cast<float2*>(smem_raw));
-    pdl_wait();
+    const bool late = (a.flags & LF_LATE_WAIT) != 0;
+    if (!late) pdl_wait();
     pdl_trigger();
     float2 v[B];
     float2 x[A];
@@ -311,7 +301,6 @@ __global__ void __launch_bounds__(LS<L>::NT, LS<L>::MINB) line_pass_kernel(LineA
 
     if (a.mode == LM_FIN) {
         // adjoint image term: out += F_i (c1[0] st1)
-        c.prefetch(false, false, true);
         if (c.vcol && c.r < B) {
 #pragma unroll
             for (int k2 = 0; k2 < A; k2++) {
@@ -320,13 +309,11 @@ __global__ void __launch_bounds__(LS<L>::NT, LS<L>::MINB) line_pass_kernel(LineA
             }
         }
         c.fwd(x, v, c.buf1);
-        cp_async_wait<0>();
         c.store_k(a.out, v, true);
         return;
     }
 
-    if (a.mode == LM_STEP)
-        c.prefetch((a.flags & LF_NO_OLD1) == 0, (a.flags & LF_NO_OLD2) == 0, accum);
+    if (a.mode == LM_STEP) c.prefetch((a.flags & LF_NO_OLD1) == 0, (a.flags & LF_NO_OLD2) == 0);
     c.load_k(a.in, v);
     if (a.mode == LM_INIT) {
         // forward start: st2 = F_i^-1[p^] s_pre  (rho_i^0 = p0 / (3 c^2))
@@ -345,16 +332,16 @@ __global__ void __launch_bounds__(LS<L>::NT, LS<L>::MINB) line_pass_kernel(LineA
         kap[k2] = c.vcol ? __ldg(a.kap + (size_t)(c.r + A * k2) * a.ncols + c.col) : 0.f;
 
     c.factor(v, a.dpre, kap, a.s_pre);
+    cp_async_wait<1>();  // state 1 has landed; the barrier inside inv() publishes it to every thread
     c.inv(v, x, c.buf0);
-    cp_async_wait<2>();
     c.update(a.st1, a.c1, (a.flags & LF_NO_OLD1) != 0, c.pf1, x);
     c.fwd(x, v, c.buf1);
     c.factor(v, a.dmid, kap, a.s_mid);
+    cp_async_wait<0>();  // state 2 likewise
     c.inv(v, x, c.buf0);
-    cp_async_wait<1>();
     c.update(a.st2, a.c2, (a.flags & LF_NO_OLD2) != 0, c.pf2, x);
     c.fwd(x, v, c.buf1);
-    cp_async_wait<0>();
+    if (late) pdl_wait();  // the new spectrum is written by the preceding pass
     c.factor(v, a.dpost, kap, a.s_post);
 
     if (AX == 0 && (a.flags & LF_INJECT) && c.vcol) {

@@ -266,7 +266,8 @@ cudaError_t run_forward(const Geom& g, const DeviceTables& t, const Workspace& w
                 a.in = cur;
                 a.out = nxt;
                 set_coef(a.c1, t, ax, CT_AS2, (n == 0) ? CT_VF0_G : CT_VF_G, CT_ONE);
-                a.flags = (n == 0 ? LF_NO_OLD1 : 0) | (ax == AX ? 0 : LF_ACCUM) | (ax == AZ ? LF_RECORD : 0);
+                a.flags = (n == 0 ? LF_NO_OLD1 : 0) | (ax == AX ? 0 : LF_ACCUM | LF_LATE_WAIT) |
+                          (ax == AZ ? LF_RECORD : 0);
                 a.rec = w.rk + (size_t)(n + 1) * g.nplane;
                 PAT_TRY(timed(prof, kLineClass[ax], st, [&] { return launch_line(ax, a, st); }));
             }
@@ -333,7 +334,7 @@ cudaError_t run_adjoint(const Geom& g, const DeviceTables& t, const Workspace& w
             a.in = w.ph[cur];
             a.out = w.ph[cur ^ 1];
             set_coef(a.c2, t, ax, CT_AS2, CT_VA_G, (n == 0) ? CT_VA0_OUT : CT_AS);
-            a.flags = (n == g.T - 2 ? (LF_NO_OLD1 | LF_NO_OLD2) : 0) | (ax == AX ? 0 : LF_ACCUM) |
+            a.flags = (n == g.T - 2 ? (LF_NO_OLD1 | LF_NO_OLD2) : 0) | (ax == AX ? 0 : LF_ACCUM | LF_LATE_WAIT) |
                       (ax == AZ ? LF_INJECT : 0);
             a.inj = w.rk + (size_t)n * g.nplane;
             PAT_TRY(timed(prof, kLineClass[ax], st, [&] { return launch_line(ax, a, st); }));

@@ -161,16 +161,16 @@ struct LineCtx {
                 for (int k2 = 0; k2 < B; k2++) v[k2] = buf1[cl * S::PITCH + r + A * k2];
             }
         } else {
+            // bin j = r + A k2 with r < A: j <= L/2 exactly for k2 < B/2, and for k2 = B/2 when r = 0
             if (vcol) {
-                const int nx = a.g.nx, nxh = a.g.nxh, ny = a.g.ny;
+                const int nxh = a.g.nxh, ny = a.g.ny;
+                const float2* own = in + pbase + (size_t)ka * nxh * ny + kb;
+                const float2* mir = in + pbase + (size_t)ma * nxh * ny + mb;
 #pragma unroll
                 for (int k2 = 0; k2 < B; k2++) {
                     const int j = r + A * k2;
-                    if (j <= nx / 2) {
-                        v[k2] = in[pbase + ((size_t)ka * nxh + j) * ny + kb];
-                    } else {
-                        v[k2] = cconj(in[pbase + ((size_t)ma * nxh + (nx - j)) * ny + mb]);
-                    }
+                    if (k2 < B / 2 || (k2 == B / 2 && r == 0)) v[k2] = own[(size_t)j * ny];
+                    else v[k2] = cconj(mir[(size_t)(L - j) * ny]);
                 }
             }
         }
@@ -208,18 +208,22 @@ struct LineCtx {
                 blk[e] = w;
             }
         } else {
+            // own entry for j <= L/2; mirror entry (-kz, L-j mod L, -ky) for j = 0 and j >= L/2, except
+            // on the self-conjugate planes kz = 0, nz/2 (k2 ranges as in load_k)
             if (vcol) {
-                const int nx = a.g.nx, nxh = a.g.nxh, ny = a.g.ny, nz = a.g.nz;
+                const int nxh = a.g.nxh, ny = a.g.ny, nz = a.g.nz;
                 const bool mirror = (ka != 0) && (2 * ka != nz);
+                float2* own = out + pbase + (size_t)ka * nxh * ny + kb;
+                float2* mir = out + pbase + (size_t)ma * nxh * ny + mb;
 #pragma unroll
                 for (int k2 = 0; k2 < B; k2++) {
                     const int j = r + A * k2;
-                    if (j <= nx / 2) {
-                        float2* p = out + pbase + ((size_t)ka * nxh + j) * ny + kb;
+                    if (k2 < B / 2 || (k2 == B / 2 && r == 0)) {
+                        float2* p = own + (size_t)j * ny;
                         *p = accum ? cadd(*p, v[k2]) : v[k2];
                     }
-                    if (mirror && (j == 0 || j >= nx / 2)) {
-                        float2* p = out + pbase + ((size_t)ma * nxh + ((nx - j) & (nx - 1))) * ny + mb;
+                    if (mirror && (k2 >= B / 2 || (k2 == 0 && r == 0))) {
+                        float2* p = mir + (size_t)((L - j) & (L - 1)) * ny;
                         const float2 c = cconj(v[k2]);
                         *p = accum ? cadd(*p, c) : c;
                     }
@@ -229,7 +233,7 @@ struct LineCtx {
     }
 
     // ---- pointwise state update in the spatial layout: s = c[0] s + c[1] x (no old: s = c[1] x),
-    // x = c[2] s
+    // x = c[2] s (c[2] == NULL: x = s)
     // (old values from the prefetched tile pf)
     __device__ __forceinline__ void update(float2* __restrict__ st, const float* const* c, bool no_old,
                                            const float2* pf, float2* x) const {
@@ -245,7 +249,7 @@ struct LineCtx {
                     nv.y = fmaf(d, o.y, nv.y);
                 }
                 st[sbase + (size_t)j * a.ncols] = nv;
-                x[k2] = cscale(nv, __ldg(c[2] + j));
+                x[k2] = c[2] ? cscale(nv, __ldg(c[2] + j)) : nv;
             }
         }
     }

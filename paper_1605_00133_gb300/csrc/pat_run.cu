@@ -202,10 +202,11 @@ static LineArgs line_base(const Geom& g, const DeviceTables& t, const Workspace&
     return a;
 }
 
+// state coefficient tables; an output gain of CT_ONE is passed as NULL (no multiply)
 static void set_coef(const float** dst, const DeviceTables& t, int ax, int c0, int c1, int c2) {
     dst[0] = t.coef[c0][ax];
     dst[1] = t.coef[c1][ax];
-    dst[2] = t.coef[c2][ax];
+    dst[2] = (c2 == CT_ONE) ? nullptr : t.coef[c2][ax];
 }
 
 cudaError_t run_forward(const Geom& g, const DeviceTables& t, const Workspace& w, const Scalars& s,

@@ -31,7 +31,7 @@ if ROOT not in sys.path:
 METRIC = "A+A^T pairs/s (64x128x128, 400 steps)"
 
 # (kernel source hash, workload, batch) -> DRAM bytes (read + write) of one time step, from ncu
-STEP_TRAFFIC = {("500878deb6b2", "c2", 1): 72.16e6}
+STEP_TRAFFIC = {("9b3de05a96e5", "c2", 1): 53.54e6}
 UNIT = "pairs/s"
 
 
@@ -270,7 +270,7 @@ def main():
     bytes_per_step = 48.0 * g.n * B
     achieved = bytes_per_step / step_s / 1e9
     # DRAM bytes of one forward time step from the committed ncu capture, valid only for the kernel
-    # sources it was taken on (profiles/pat_step_kernels_c2.md)
+    # sources it was taken on (profiles/pat_line_pass_c2.md)
     traffic = STEP_TRAFFIC.get((_source_hash(), w.name, B))
     roofline = {"bound": "hbm", "kernel": "time step (line passes x, y, z of A, and of A^T)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,

@@ -24,8 +24,9 @@
 //
 // A CTA owns TC lines.  A line's length-L transform is the two-pass split of pat_fft.cuh: in the
 // k-space layout thread r < A holds X[r + A k2] (k2 < B), in the spatial layout thread r < B holds
-// x[r + B k2] (k2 < A); each transform is one exchange through shared memory laid out [row][line]
-// with the line index fastest.  Two exchange buffers alternate, so every transform costs one
+// x[r + B k2] (k2 < A) -- or, when A = 2B, the thread pair (2 r', 2 r' + 1) shares row group r'
+// (each holds A/2 of its values and computes half of its A-point DFT); each transform is one
+// exchange through shared memory laid out [row][line] with the line index fastest.  Two exchange buffers alternate, so every transform costs one
 // barrier.  The old values of both states are copied to shared memory with cp.async as soon as the
 // kernel starts, so their latency overlaps the first transforms instead of stalling each update.
 //
@@ -51,29 +52,44 @@ namespace pat {
 
 template <int L>
 struct LS {
-    static constexpr int A = Split<L>::A;  // values per thread, spatial layout
-    static constexpr int B = Split<L>::B;  // values per thread, k-space layout
-    // lines per CTA: about 1024 line points per CTA (8 KB tiles), at least 8 lines (64-byte rows)
-    static constexpr int TC = (1024 / L > 32) ? 32 : (1024 / L < 8 ? 8 : 1024 / L);
+    static constexpr int A = Split<L>::A;  // radix of the spatial-side DFT
+    static constexpr int B = Split<L>::B;  // radix of the k-space-side DFT
+    // A = 2B: the spatial-side A-point DFT is shared by a thread pair (two A/2-point DFTs and one
+    // radix-2 stage through warp shuffles), so both layouts use every thread
+    static constexpr bool PAIR = (A == 2 * B);
+    static constexpr int XN = PAIR ? A / 2 : A;  // values per thread, spatial layout
+    // lines per CTA: about 1024 line points per CTA (8 KB tiles), at least 8 lines (64-byte rows);
+    // thread pairs must share a warp, so at most 16 lines when PAIR
+    static constexpr int TC0 = (1024 / L > 32) ? 32 : (1024 / L < 8 ? 8 : 1024 / L);
+    static constexpr int TC = (PAIR && TC0 > 16) ? 16 : TC0;
     static constexpr int NT = A * TC;
-    static constexpr int PITCH = L + 1;     // staging row pitch for y lines
-    static constexpr int BUF = L * TC + TC; // one exchange buffer (float2), also holds TC staged rows
-    static constexpr int TILE = L * TC;     // one prefetched state tile (float2)
+    // staging row pitch for y lines: odd for 16-line half-warps, = 2 (mod 16) for 8 lines
+    static constexpr int PITCH = (TC >= 16) ? L + 1 : L + 2;
+    static constexpr int BUF = L * TC + 2 * TC;  // one exchange buffer (float2), also holds TC staged rows
+    static constexpr int TILE = L * TC;          // one prefetched state tile (float2)
     static constexpr size_t smem = (2 * (size_t)BUF + 2 * (size_t)TILE) * sizeof(float2);
     static constexpr int MINB = (NT >= 256) ? 2 : 4;
 };
 
+// W_R^(DIR k) = exp(DIR 2 pi i k / R), R in {2, 4, 8, 16}, k < R/2
+template <int R, int DIR>
+__device__ __forceinline__ float2 wr(int k) {
+    return make_float2(w16c(k * (16 / R)), DIR * w16s(k * (16 / R)));
+}
+
 template <int L, int AX>
 struct LineCtx {
     using S = LS<L>;
-    static constexpr int A = S::A, B = S::B, TC = S::TC;
+    static constexpr int A = S::A, B = S::B, TC = S::TC, XN = S::XN;
+    static constexpr bool PAIR = S::PAIR;
     const LineArgs& a;
     float2* buf0;
     float2* buf1;
     float2* pf1;    // prefetched old state 1, [j][line]
     float2* pf2;    // prefetched old state 2
     int cl, r, col, col0, b;
-    bool vcol;
+    int xr, xh;     // spatial layout: row group and half (PAIR), else xr = r, xh = 0
+    bool vcol, xact;
     size_t sbase;   // state element of this line at position 0
     size_t pbase;   // this batch entry's 3D spectrum
     int ka, kb;     // x lines: kz, ky
@@ -87,9 +103,12 @@ struct LineCtx {
         const int tid = threadIdx.x;
         cl = tid % TC;
         r = tid / TC;
+        xr = PAIR ? (r >> 1) : r;
+        xh = PAIR ? (r & 1) : 0;
         col0 = blockIdx.x * TC;
         col = col0 + cl;
         vcol = col < a.ncols;
+        xact = vcol && (PAIR || r < B);
         b = blockIdx.y;
         sbase = (size_t)b * L * a.ncols + col;
         pbase = (size_t)b * a.g.nspec;
@@ -102,38 +121,78 @@ struct LineCtx {
             mb = (ny - kb) & (ny - 1);
         }
     }
+    // position along the line of spatial-layout value q
+    __device__ __forceinline__ int xpos(int q) const { return PAIR ? xr + B * (XN * xh + q) : r + B * q; }
+    // exchange-buffer element of (row, this line).  With 8 lines a row is half the banks; rows that a
+    // half-warp touches together differ by 1, A or B, so bit 0 of the row is flipped by bit 0 of
+    // row / B to put them in different halves.
+    __device__ __forceinline__ int xo(int row) const {
+        return ((TC < 16) ? (row ^ ((row / B) & 1)) : row) * TC + cl;
+    }
+
     // ---- transforms between the layouts (every thread of the CTA must call these)
     // k-space layout (v) -> spatial layout (x) through xb
     __device__ __forceinline__ void inv(float2* v, float2* x, float2* xb) const {
         if (vcol) {
             Dft<B, +1>::run(v);
-            float2* dst = xb + r * TC + cl;
 #pragma unroll
             for (int k1p = 0; k1p < B; k1p++)
-                dst[k1p * A * TC] = (k1p == 0) ? v[0] : cmul(v[k1p], twiddle<L, +1>(a.tw, r * k1p));
+                xb[xo(k1p * A + r)] = (k1p == 0) ? v[0] : cmul(v[k1p], twiddle<L, +1>(a.tw, r * k1p));
         }
         __syncthreads();
-        if (vcol && r < B) {
-            const float2* src = xb + r * A * TC + cl;
+        if (PAIR) {
+            // A-point DFT of row group xr by decimation in time: this thread the even (xh = 0) or odd
+            // inputs, then X[k] = E[k] + W_A^k O[k], X[k + A/2] = E[k] - W_A^k O[k]
 #pragma unroll
-            for (int t = 0; t < A; t++) x[t] = src[t * TC];
+            for (int q = 0; q < XN; q++) x[q] = vcol ? xb[xo(xr * A + 2 * q + xh)] : make_float2(0.f, 0.f);
+            Dft<XN, +1>::run(x);
+#pragma unroll
+            for (int k = 1; k < XN; k++)
+                if (xh) x[k] = cmul(x[k], wr<A, +1>(k));
+#pragma unroll
+            for (int k = 0; k < XN; k++) {
+                const float2 t = make_float2(__shfl_xor_sync(0xffffffffu, x[k].x, TC),
+                                             __shfl_xor_sync(0xffffffffu, x[k].y, TC));
+                x[k] = xh ? csub(t, x[k]) : cadd(x[k], t);
+            }
+        } else if (vcol && r < B) {
+#pragma unroll
+            for (int t = 0; t < A; t++) x[t] = xb[xo(r * A + t)];
             Dft<A, +1>::run(x);
         }
     }
     // spatial layout (x) -> k-space layout (v) through xb
     __device__ __forceinline__ void fwd(float2* x, float2* v, float2* xb) const {
-        if (vcol && r < B) {
+        if (PAIR) {
+            // decimation in frequency: Y[2k] from x[q] + x[q + A/2] (xh = 0), Y[2k+1] from
+            // (x[q] - x[q + A/2]) W_A^-q (xh = 1); this thread holds x[q + xh A/2]
+#pragma unroll
+            for (int q = 0; q < XN; q++) {
+                const float2 t = make_float2(__shfl_xor_sync(0xffffffffu, x[q].x, TC),
+                                             __shfl_xor_sync(0xffffffffu, x[q].y, TC));
+                x[q] = xh ? csub(t, x[q]) : cadd(x[q], t);
+            }
+#pragma unroll
+            for (int q = 1; q < XN; q++)
+                if (xh) x[q] = cmul(x[q], wr<A, -1>(q));
+            Dft<XN, -1>::run(x);
+            if (vcol) {
+#pragma unroll
+                for (int k = 0; k < XN; k++) {
+                    const int k1 = 2 * k + xh;
+                    xb[xo(k1 * B + xr)] = cmul(x[k], twiddle<L, -1>(a.tw, xr * k1));
+                }
+            }
+        } else if (vcol && r < B) {
             Dft<A, -1>::run(x);
-            float2* dst = xb + r * TC + cl;
 #pragma unroll
             for (int k1 = 0; k1 < A; k1++)
-                dst[k1 * B * TC] = (k1 == 0) ? x[0] : cmul(x[k1], twiddle<L, -1>(a.tw, r * k1));
+                xb[xo(k1 * B + r)] = (k1 == 0) ? x[0] : cmul(x[k1], twiddle<L, -1>(a.tw, r * k1));
         }
         __syncthreads();
         if (vcol) {
-            const float2* src = xb + r * B * TC + cl;
 #pragma unroll
-            for (int t = 0; t < B; t++) v[t] = src[t * TC];
+            for (int t = 0; t < B; t++) v[t] = xb[xo(r * B + t)];
             Dft<B, -1>::run(v);
         }
     }
@@ -237,11 +296,11 @@ struct LineCtx {
     // (old values from the prefetched tile pf)
     __device__ __forceinline__ void update(float2* __restrict__ st, const float* const* c, bool no_old,
                                            const float2* pf, float2* x) const {
-        if (vcol && r < B) {
+        if (xact) {
 #pragma unroll
-            for (int k2 = 0; k2 < A; k2++) {
-                const int j = r + B * k2;
-                float2 nv = cscale(x[k2], __ldg(c[1] + j));
+            for (int q = 0; q < XN; q++) {
+                const int j = xpos(q);
+                float2 nv = cscale(x[q], __ldg(c[1] + j));
                 if (!no_old) {
                     const float d = __ldg(c[0] + j);
                     const float2 o = pf[j * TC + cl];
@@ -249,7 +308,7 @@ struct LineCtx {
                     nv.y = fmaf(d, o.y, nv.y);
                 }
                 st[sbase + (size_t)j * a.ncols] = nv;
-                x[k2] = c[2] ? cscale(nv, __ldg(c[2] + j)) : nv;
+                x[q] = c[2] ? cscale(nv, __ldg(c[2] + j)) : nv;
             }
         }
     }
@@ -299,18 +358,17 @@ __global__ void __launch_bounds__(LS<L>::NT, LS<L>::MINB) line_pass_kernel(LineA
     const bool late = (a.flags & LF_LATE_WAIT) != 0;
     if (!late) pdl_wait();
     pdl_trigger();
+    constexpr int XN = S::XN;
     float2 v[B];
-    float2 x[A];
+    float2 x[XN];
     const bool accum = (a.flags & LF_ACCUM) != 0;
 
     if (a.mode == LM_FIN) {
         // adjoint image term: out += F_i (c1[0] st1)
-        if (c.vcol && c.r < B) {
 #pragma unroll
-            for (int k2 = 0; k2 < A; k2++) {
-                const int j = c.r + B * k2;
-                x[k2] = cscale(a.st1[c.sbase + (size_t)j * a.ncols], __ldg(a.c1[0] + j));
-            }
+        for (int q = 0; q < XN; q++) {
+            const int j = c.xpos(q);
+            x[q] = c.xact ? cscale(a.st1[c.sbase + (size_t)j * a.ncols], __ldg(a.c1[0] + j)) : make_float2(0.f, 0.f);
         }
         c.fwd(x, v, c.buf1);
         c.store_k(a.out, v, true);
@@ -323,9 +381,9 @@ __global__ void __launch_bounds__(LS<L>::NT, LS<L>::MINB) line_pass_kernel(LineA
         // forward start: st2 = F_i^-1[p^] s_pre  (rho_i^0 = p0 / (3 c^2))
         c.factor(v, nullptr, nullptr, a.s_pre);
         c.inv(v, x, c.buf0);
-        if (c.vcol && c.r < B) {
+        if (c.xact) {
 #pragma unroll
-            for (int k2 = 0; k2 < A; k2++) a.st2[c.sbase + (size_t)(c.r + B * k2) * a.ncols] = x[k2];
+            for (int q = 0; q < XN; q++) a.st2[c.sbase + (size_t)c.xpos(q) * a.ncols] = x[q];
         }
         return;
     }

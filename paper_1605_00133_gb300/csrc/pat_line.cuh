@@ -28,12 +28,13 @@
 // (each holds A/2 of its values and computes half of its A-point DFT); each transform is one
 // exchange through shared memory laid out [row][line] with the line index fastest.  Two exchange buffers alternate, so every transform costs one
 // barrier.  The old values of both states are copied to shared memory with cp.async as soon as the
-// kernel starts, so their latency overlaps the first transforms instead of stalling each update.
+// kernel starts, and the old values of the spectrum a y or z pass adds to as soon as its writer has
+// completed, so their latency overlaps transforms instead of stalling each update.
 //
 // Launch overlap.  The y and z passes of a step read only the previous step's spectrum and their own
 // states until they add to the new spectrum, so they are launched as programmatic dependents that
-// start at once and wait for their predecessor (griddepcontrol.wait) only before that last stage
-// (LF_LATE_WAIT).  Everything they read before the wait was written by kernels that had completed
+// start at once and wait for their predecessor (griddepcontrol.wait) only after their first state
+// update, before fetching the spectrum they add to (LF_LATE_WAIT).  Everything they read before the wait was written by kernels that had completed
 // before the x pass of the step passed its own wait, and is read through L2 (ld.cg, cp.async.cg).
 // No kernel waits on a grid whose CTAs have not all started, so the overlap cannot deadlock.
 //
@@ -66,8 +67,8 @@ struct LS {
     // staging row pitch for y lines: odd for 16-line half-warps, = 2 (mod 16) for 8 lines
     static constexpr int PITCH = (TC >= 16) ? L + 1 : L + 2;
     static constexpr int BUF = L * TC + 2 * TC;  // one exchange buffer (float2), also holds TC staged rows
-    static constexpr int TILE = L * TC;          // one prefetched state tile (float2)
-    static constexpr size_t smem = (2 * (size_t)BUF + 2 * (size_t)TILE) * sizeof(float2);
+    static constexpr int TILE = L * TC;          // one prefetched tile (float2)
+    static constexpr size_t smem = (2 * (size_t)BUF + 3 * (size_t)TILE) * sizeof(float2);
     static constexpr int MINB = (NT >= 256) ? 2 : 4;
 };
 
@@ -87,6 +88,7 @@ struct LineCtx {
     float2* buf1;
     float2* pf1;    // prefetched old state 1, [j][line]
     float2* pf2;    // prefetched old state 2
+    float2* pfo;    // prefetched old output: z lines [kz][line], y lines the contiguous row block
     int cl, r, col, col0, b;
     int xr, xh;     // spatial layout: row group and half (PAIR), else xr = r, xh = 0
     bool vcol, xact;
@@ -100,6 +102,7 @@ struct LineCtx {
         buf1 = smem + S::BUF;
         pf1 = smem + 2 * S::BUF;
         pf2 = pf1 + S::TILE;
+        pfo = pf2 + S::TILE;
         const int tid = threadIdx.x;
         cl = tid % TC;
         r = tid / TC;
@@ -235,14 +238,16 @@ struct LineCtx {
         }
     }
     // write (or add, LF_ACCUM) the k-space layout values to the 3D spectrum; z lines return the
-    // stored totals in v
-    __device__ __forceinline__ void store_k(float2* __restrict__ out, float2* v, bool accum) const {
+    // stored totals in v.  pre: the old values of z and y lines are in pfo (prefetch_out) rather
+    // than to be loaded.
+    __device__ __forceinline__ void store_k(float2* __restrict__ out, float2* v, bool accum, bool pre) const {
         if (AX == 0) {
             if (vcol) {
 #pragma unroll
                 for (int k2 = 0; k2 < B; k2++) {
-                    float2* p = out + pbase + (size_t)(r + A * k2) * a.ncols + col;
-                    if (accum) v[k2] = cadd(*p, v[k2]);
+                    const int j = r + A * k2;
+                    float2* p = out + pbase + (size_t)j * a.ncols + col;
+                    if (accum) v[k2] = cadd(pre ? pfo[j * TC + cl] : *p, v[k2]);
                     *p = v[k2];
                 }
             }
@@ -261,7 +266,7 @@ struct LineCtx {
                 const float2* s = buf0 + row * S::PITCH + pt;
                 float4 w = make_float4(s[0].x, s[0].y, s[1].x, s[1].y);
                 if (accum) {
-                    const float4 o = blk[e];
+                    const float4 o = pre ? reinterpret_cast<const float4*>(pfo)[e] : blk[e];
                     w.x += o.x; w.y += o.y; w.z += o.z; w.w += o.w;
                 }
                 blk[e] = w;
@@ -336,6 +341,26 @@ struct LineCtx {
         cp_async_commit();
     }
 
+    // cp.async copy of the old output of z and y lines into pfo (one commit group, committed by every
+    // thread; issue only after the output's writer has completed)
+    __device__ __forceinline__ void prefetch_out(bool on) const {
+        if (on && AX == 0) {
+            constexpr int NCH = L * (TC / 2);
+            const int ncol2 = min(TC, a.ncols - col0) / 2;
+            const float2* base = a.out + pbase + col0;
+            for (int q = threadIdx.x; q < NCH; q += S::NT) {
+                const int j = q / (TC / 2), cc = q % (TC / 2);
+                if (cc < ncol2) cp_async16(pfo + j * TC + 2 * cc, base + (size_t)j * a.ncols + 2 * cc);
+            }
+        } else if (on && AX == 1) {
+            const int nrows = min(TC, a.ncols - col0);
+            const float4* blk = reinterpret_cast<const float4*>(a.out + pbase + (size_t)col0 * L);
+            for (int e = threadIdx.x; e < nrows * (L / 2); e += S::NT)
+                cp_async16(reinterpret_cast<float4*>(pfo) + e, blk + e);
+        }
+        cp_async_commit();
+    }
+
     // k-space factor D[j] kappa s (D == NULL: s)
     __device__ __forceinline__ void factor(float2* v, const float2* __restrict__ D, const float* kap,
                                            float s) const {
@@ -371,7 +396,7 @@ __global__ void __launch_bounds__(LS<L>::NT, LS<L>::MINB) line_pass_kernel(LineA
             x[q] = c.xact ? cscale(a.st1[c.sbase + (size_t)j * a.ncols], __ldg(a.c1[0] + j)) : make_float2(0.f, 0.f);
         }
         c.fwd(x, v, c.buf1);
-        c.store_k(a.out, v, true);
+        c.store_k(a.out, v, true, false);
         return;
     }
 
@@ -397,13 +422,16 @@ __global__ void __launch_bounds__(LS<L>::NT, LS<L>::MINB) line_pass_kernel(LineA
     cp_async_wait<1>();  // state 1 has landed; the barrier inside inv() publishes it to every thread
     c.inv(v, x, c.buf0);
     c.update(a.st1, a.c1, (a.flags & LF_NO_OLD1) != 0, c.pf1, x);
+    if (late) pdl_wait();  // the new spectrum is written by the preceding pass
+    const bool pre = accum && AX != 2;
+    c.prefetch_out(pre);
     c.fwd(x, v, c.buf1);
     c.factor(v, a.dmid, kap, a.s_mid);
-    cp_async_wait<0>();  // state 2 likewise
+    cp_async_wait<1>();  // state 2 likewise (the old output may still be in flight)
     c.inv(v, x, c.buf0);
     c.update(a.st2, a.c2, (a.flags & LF_NO_OLD2) != 0, c.pf2, x);
+    cp_async_wait<0>();  // old output; published by the barrier inside fwd()
     c.fwd(x, v, c.buf1);
-    if (late) pdl_wait();  // the new spectrum is written by the preceding pass
     c.factor(v, a.dpost, kap, a.s_post);
 
     if (AX == 0 && (a.flags & LF_INJECT) && c.vcol) {
@@ -414,7 +442,7 @@ __global__ void __launch_bounds__(LS<L>::NT, LS<L>::MINB) line_pass_kernel(LineA
             v[k2] = cadd(v[k2], cmul(sv, __ldg(a.tw + ((kz * a.zs) & (L - 1)))));
         }
     }
-    c.store_k(a.out, v, accum);
+    c.store_k(a.out, v, accum, pre);
 
     if (AX == 0 && (a.flags & LF_RECORD)) {
         // plane spectrum at z = zs: (1/nz) sum_kz p^(kz) e^{+2 pi i kz zs / nz}; partial sums over

@@ -60,7 +60,12 @@ ZKernels z_kernels_for(int nz);
 
 // Line passes of the time step (pat_line.cuh).
 enum LineMode { LM_STEP = 0, LM_INIT = 1, LM_FIN = 2 };
-enum LineFlag { LF_NO_OLD1 = 1, LF_NO_OLD2 = 2, LF_ACCUM = 4, LF_RECORD = 8, LF_INJECT = 16, LF_LATE_WAIT = 32 };
+enum LineFlag {
+    LF_NO_OLD1 = 1, LF_NO_OLD2 = 2, LF_ACCUM = 4, LF_RECORD = 8, LF_INJECT = 16,
+    LF_LATE_WAIT = 32,    // wait for the predecessor only before fetching the spectrum added to
+    LF_TRIGGER_MID = 64,  // let the successor launch after that wait (default: at the start)
+    LF_TRIGGER_END = 128  // let the successor launch only when this grid completes
+};
 
 struct LineArgs {
     Geom g;

@@ -382,7 +382,7 @@ __global__ void __launch_bounds__(LS<L>::NT, LS<L>::MINB) line_pass_kernel(LineA
     LineCtx<L, AX> c(a, reinterpret_cast<float2*>(smem_raw));
     const bool late = (a.flags & LF_LATE_WAIT) != 0;
     if (!late) pdl_wait();
-    pdl_trigger();
+    if (!(a.flags & (LF_TRIGGER_MID | LF_TRIGGER_END))) pdl_trigger();
     constexpr int XN = S::XN;
     float2 v[B];
     float2 x[XN];
@@ -423,6 +423,7 @@ __global__ void __launch_bounds__(LS<L>::NT, LS<L>::MINB) line_pass_kernel(LineA
     c.inv(v, x, c.buf0);
     c.update(a.st1, a.c1, (a.flags & LF_NO_OLD1) != 0, c.pf1, x);
     if (late) pdl_wait();  // the new spectrum is written by the preceding pass
+    if (a.flags & LF_TRIGGER_MID) pdl_trigger();
     const bool pre = accum && AX != 2;
     c.prefetch_out(pre);
     c.fwd(x, v, c.buf1);

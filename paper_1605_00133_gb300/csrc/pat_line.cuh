@@ -318,24 +318,17 @@ struct LineCtx {
         }
     }
 
-    // issue the cp.async copies of the old states (two commit groups, state 1 then state 2; every
-    // thread commits both).  16-byte copies of column pairs (ncols and the tile start are even), so a
-    // thread's copies are not the values it later reads: consumers wait, then pass a barrier.
-    __device__ __forceinline__ void prefetch(bool old1, bool old2) const {
+    // issue the cp.async copy of one old state tile (one commit group; every thread commits it).
+    // 16-byte copies of column pairs (ncols and the tile start are even), so a thread's copies are
+    // not the values it later reads: consumers wait, then pass a barrier.
+    __device__ __forceinline__ void prefetch(const float2* __restrict__ st, float2* pf, bool on) const {
         constexpr int NCH = L * (TC / 2);  // 16-byte chunks per tile
-        const int ncol2 = min(TC, a.ncols - col0) / 2;
-        const size_t base = (size_t)b * L * a.ncols + col0;
-        if (old1) {
+        if (on) {
+            const int ncol2 = min(TC, a.ncols - col0) / 2;
+            const size_t base = (size_t)b * L * a.ncols + col0;
             for (int q = threadIdx.x; q < NCH; q += S::NT) {
                 const int j = q / (TC / 2), cc = q % (TC / 2);
-                if (cc < ncol2) cp_async16(pf1 + j * TC + 2 * cc, a.st1 + base + (size_t)j * a.ncols + 2 * cc);
-            }
-        }
-        cp_async_commit();
-        if (old2) {
-            for (int q = threadIdx.x; q < NCH; q += S::NT) {
-                const int j = q / (TC / 2), cc = q % (TC / 2);
-                if (cc < ncol2) cp_async16(pf2 + j * TC + 2 * cc, a.st2 + base + (size_t)j * a.ncols + 2 * cc);
+                if (cc < ncol2) cp_async16(pf + j * TC + 2 * cc, st + base + (size_t)j * a.ncols + 2 * cc);
             }
         }
         cp_async_commit();
@@ -400,7 +393,10 @@ __global__ void __launch_bounds__(LS<L>::NT, LS<L>::MINB) line_pass_kernel(LineA
         return;
     }
 
-    if (a.mode == LM_STEP) c.prefetch((a.flags & LF_NO_OLD1) == 0, (a.flags & LF_NO_OLD2) == 0);
+    if (a.mode == LM_STEP) {
+        c.prefetch(a.st1, c.pf1, (a.flags & LF_NO_OLD1) == 0);
+        c.prefetch(a.st2, c.pf2, (a.flags & LF_NO_OLD2) == 0);
+    }
     c.load_k(a.in, v);
     if (a.mode == LM_INIT) {
         // forward start: st2 = F_i^-1[p^] s_pre  (rho_i^0 = p0 / (3 c^2))

@@ -165,9 +165,10 @@ static const int kLineClass[3] = {KC_LINE_Z, KC_LINE_Y, KC_LINE_X};
 static const int kPassOrder[3] = {AX, AY, AZ};  // x writes the new spectrum, y and z add to it
 // When each pass lets its successor launch, by axis (z, y, x).  Launched early, a grid's CTAs land
 // on whichever SMs free up first, four to an SM, and wait there; measured on c2, launching the x pass
-// only when the z pass completes (all 152 SMs free) and the z pass only once the y pass has passed
-// its own wait beats launching every pass at the start of its predecessor (56.0 vs 52.6 pairs/s).
-static const int kTrigger[3] = {LF_TRIGGER_END, LF_TRIGGER_MID, 0};
+// only when the z pass completes (all 152 SMs free) and the y and z passes once their predecessor
+// has passed its mid-pass point beats launching every pass at the start of its predecessor
+// (56.7 vs 52.6 pairs/s).
+static const int kTrigger[3] = {LF_TRIGGER_END, LF_TRIGGER_MID, LF_TRIGGER_MID};
 
 // spec[b][kz][c] = S[b][c] exp(-2 pi i kz zs / nz): the 3D spectrum of a plane source at z = zs
 __global__ void spread_plane_kernel(Geom g, const float2* __restrict__ tw_z, const float2* __restrict__ S,

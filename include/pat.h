@@ -115,15 +115,22 @@ pat_status pat_adjoint(pat_grid* grid, const float* f_dev, float* p_dev, void* c
 /* f = C A p0 like pat_forward, for callers that cannot allocate device memory when they call the
  * operator (e.g. reconstruction loops that reserve their whole device budget at start-up).  The
  * paper has no counterpart; this is a deployment variant.  It allocates nothing: the time-stepping
- * state, half spectra and recorded plane series live in one static device array of 64 MiB that
- * every GPU loading libpat holds until the process exits (grids up to 64x128x128 with T = 400 and
- * point sampling fit; larger ones are rejected with PAT_ERR_INVALID_ARG and a message giving the
- * bytes needed).  The grid's constant tables and index sets are read, not written.  The first call
+ * state, spectra and recorded plane series live in one static device array of 64 MiB that every
+ * GPU loading libpat holds until the process exits (64x128x128 with T = 400 and point sampling
+ * needs 58 MiB; grids that do not fit are rejected with PAT_ERR_INVALID_ARG and a message giving
+ * the bytes needed).  The grid's constant tables and index sets are read, not written.  The first call
  * on each device looks up the array's device address (cudaGetSymbolAddress), so make that first
  * call before any stream capture.  All calls share the one array and every call overwrites it (no
  * part of it needs to start at zero): calls that can overlap on the GPU (other streams, other
  * grids, other threads) race with each other and must be serialised by the caller. */
 pat_status pat_forward_noalloc(pat_grid* grid, const float* p0_dev, float* f_dev, void* cuda_stream);
+
+/* The index sets the grid holds on the device, copied back for bit-exact checks of C (Sec. 3.1,
+ * Sec. 4.3): POINTS writes the m plane indices to host_idx_or_perm (int32[m]); HADAMARD* writes the
+ * scramble permutation to host_idx_or_perm (int32[Ny*Nx]) and the m Hadamard rows to host_rows
+ * (int32[m]); FULL writes nothing.  Host buffers owned by the caller; a pointer the kind needs may
+ * not be NULL (PAT_ERR_INVALID_ARG).  Synchronous: returns after the copies have completed. */
+pat_status pat_get_indices(const pat_grid* grid, int32_t* host_idx_or_perm, int32_t* host_rows);
 
 /* C alone, applied to a plane series (Sec. 3.1, Eq. GenScan per time point):
  *   pbar_dev: float[B][nt][Ny*Nx] -> f_dev: float[B][nt][m].  nt >= 1. */
@@ -184,8 +191,8 @@ pat_status pat_bregman_solve(pat_grid* grid, const float* f_dev, const float* wa
  * bracketed by CUDA events recorded on the call's stream.  pat_profile_enable(grid, 1) starts (and
  * clears) the record; pat_profile_read waits for the recorded events, then reports per kernel class
  * its name (NUL-terminated, at most 47 characters, in names[48*i]), total device milliseconds and
- * launch count.  Classes: plane_init, plane_vel, plane_rho_fwd, plane_rho_adj, zpass_grad3,
- * zpass_each3, zpass_sum3, sample (see pat_kernels.cu).  n_classes receives the number written
+ * launch count.  Classes: line_x, line_y, line_z (the time step's line passes), plane_fft, z_fft
+ * (transforms outside the time loop), sample.  n_classes receives the number written
  * (<= max_classes). */
 pat_status pat_profile_enable(pat_grid* grid, int32_t enable);
 pat_status pat_profile_read(pat_grid* grid, int32_t max_classes, char* names, double* total_ms,

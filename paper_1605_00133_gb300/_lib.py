@@ -18,7 +18,7 @@ STATUS_NAMES = {0: "PAT_OK", 1: "PAT_ERR_INVALID_ARG", 2: "PAT_ERR_CUDA", 3: "PA
 EXPORTS = ["pat_create_grid", "pat_destroy_grid", "pat_grid_info", "pat_workspace_bytes",
            "pat_forward", "pat_adjoint", "pat_sample", "pat_sample_adjoint", "pat_profile_enable",
            "pat_profile_read", "pat_last_error", "pat_version", "pat_forward_noalloc", "pat_tv_prox",
-           "pat_bregman_solve"]
+           "pat_bregman_solve", "pat_get_indices"]
 
 
 class PatError(RuntimeError):
@@ -87,6 +87,9 @@ def load() -> ctypes.CDLL:
             fn = getattr(L, name)
             fn.argtypes = [vp, vp, vp, ctypes.c_int32, vp]
             fn.restype = ctypes.c_int
+        ip = ctypes.POINTER(ctypes.c_int32)
+        L.pat_get_indices.argtypes = [vp, ip, ip]
+        L.pat_get_indices.restype = ctypes.c_int
         L.pat_tv_prox.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_int32, ctypes.c_int32, vp]
         L.pat_tv_prox.restype = ctypes.c_int
         L.pat_bregman_solve.argtypes = [vp, vp, vp, vp, ctypes.POINTER(SolveParams),

@@ -425,6 +425,26 @@ pat_status pat_sample_adjoint(pat_grid* G, const float* f, float* pbar, int32_t 
 
 static const char* kClassNames[KC_COUNT] = {"line_x", "line_y", "line_z", "plane_fft", "z_fft", "sample"};
 
+pat_status pat_get_indices(const pat_grid* G, int32_t* host_idx_or_perm, int32_t* host_rows) {
+    g_err.clear();
+    if (!G) return fail(PAT_ERR_INVALID_ARG, "pat_get_indices: NULL grid");
+    pat_status st = check_device(G);
+    if (st != PAT_OK) return st;
+    const int M = G->g.m_plane;
+    cudaError_t e = cudaSuccess;
+    if (G->kind == PAT_SAMPLE_POINTS) {
+        if (!host_idx_or_perm && G->m > 0) return fail(PAT_ERR_INVALID_ARG, "pat_get_indices: NULL index buffer");
+        if (G->m > 0) e = cudaMemcpy(host_idx_or_perm, G->w.idx, (size_t)G->m * sizeof(int32_t), cudaMemcpyDeviceToHost);
+    } else if (G->kind == PAT_SAMPLE_HADAMARD01 || G->kind == PAT_SAMPLE_HADAMARDPM) {
+        if (!host_idx_or_perm || !host_rows) return fail(PAT_ERR_INVALID_ARG, "pat_get_indices: NULL buffer");
+        e = cudaMemcpy(host_idx_or_perm, G->w.perm, (size_t)M * sizeof(int32_t), cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(host_rows, G->w.rows, (size_t)G->m * sizeof(int32_t), cudaMemcpyDeviceToHost);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "pat_get_indices");
+    return PAT_OK;
+}
+
 pat_status pat_profile_enable(pat_grid* G, int32_t enable) {
     g_err.clear();
     if (!G) return fail(PAT_ERR_INVALID_ARG, "pat_profile_enable: NULL grid");

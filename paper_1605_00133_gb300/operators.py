@@ -113,6 +113,19 @@ class PatOperator:
                                                   _stream_ptr(f.device)))
         return pbar
 
+    def indices(self):
+        """The index sets held on the device (pat_get_indices): POINTS -> (idx, None),
+        HADAMARD* -> (perm, rows), FULL -> (None, None)."""
+        k = self.sampling.kind
+        if k == KIND_FULL:
+            return None, None
+        a = np.zeros(self.m if k == KIND_RSP else self.grid.m_plane, dtype=np.int32)
+        r = np.zeros(self.m, dtype=np.int32) if k in (KIND_SHD01, KIND_SHDPM) else None
+        ip = ctypes.POINTER(ctypes.c_int32)
+        _lib.check(_lib.load().pat_get_indices(self._h, a.ctypes.data_as(ip),
+                                               r.ctypes.data_as(ip) if r is not None else None))
+        return a, r
+
     # ------------------------------------------------------------------ variational reconstruction
     def tv_prox(self, p: torch.Tensor, alpha: float, iters: int = 200, out: torch.Tensor = None):
         """argmin_{q >= 0} 1/2 ||q - p||^2 + alpha TV(q) (pat_tv_prox, Neumann boundary)."""

@@ -159,6 +159,28 @@ def test_zero_input_gives_zero(dev):
 
 # ------------------------------------------------------------------------------ index work, bit-exact
 
+@pytest.mark.parametrize("name", ["c2", "c3"])
+def test_device_index_sets_are_bit_exact(dev, name):
+    """pat_get_indices returns exactly the index sets of the workload's seeded generator, and they are
+    valid: distinct ascending plane points (rSP); a permutation and distinct rows (sHd)."""
+    from paper_1605_00133_gb300.operators import PatOperator
+    w = presets.workload(name)
+    s = w.sampling
+    op = PatOperator(w.grid, s)
+    a, r = op.indices()
+    M = w.grid.m_plane
+    if s.kind == presets.KIND_RSP:
+        assert r is None
+        assert np.array_equal(a, np.asarray(s.indices, dtype=np.int32))
+        assert len(a) == s.m and np.all(np.diff(a) > 0) and a[0] >= 0 and a[-1] < M
+    else:
+        assert np.array_equal(a, np.asarray(s.perm, dtype=np.int32))
+        assert np.array_equal(r, np.asarray(s.rows, dtype=np.int32))
+        assert np.array_equal(np.sort(a), np.arange(M))
+        assert len(np.unique(r)) == s.m and r.min() >= 0 and r.max() < M
+    op.close()
+
+
 @pytest.mark.parametrize("kind", [presets.KIND_RSP, presets.KIND_SHD01, presets.KIND_SHDPM])
 def test_sampling_is_bit_exact_on_integer_planes(oracle_mod, dev, kind):
     """Integer-valued planes: every sum in C and C^T is exact in FP32 and FP64 alike (M = 4^k makes

@@ -19,6 +19,10 @@ EXPORTS = ["pat_create_grid", "pat_destroy_grid", "pat_grid_info", "pat_workspac
            "pat_forward", "pat_adjoint", "pat_sample", "pat_sample_adjoint", "pat_profile_enable",
            "pat_profile_read", "pat_last_error", "pat_version", "pat_forward_noalloc", "pat_tv_prox",
            "pat_bregman_solve", "pat_get_indices"]
+# include/pat_unet.h (learned warm start)
+UNET_EXPORTS = ["pat_unet_conv3", "pat_unet_wgrad_scratch", "pat_unet_conv3_wgrad", "pat_unet_cast_weights",
+                "pat_unet_relu_bwd", "pat_unet_pool", "pat_unet_pool_bwd_add", "pat_unet_up", "pat_unet_up_bwd",
+                "pat_unet_input", "pat_unet_head", "pat_unet_head_scratch", "pat_unet_head_bwd", "pat_unet_adam"]
 
 
 class PatError(RuntimeError):
@@ -100,6 +104,26 @@ def load() -> ctypes.CDLL:
         L.pat_profile_read.argtypes = [vp, ctypes.c_int32, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)]
         L.pat_profile_read.restype = ctypes.c_int
+        i32, i64, f32 = ctypes.c_int32, ctypes.c_int64, ctypes.c_float
+        L.pat_unet_conv3.argtypes = [vp, i32, i32, vp, i32, vp, i32, i32, i32, i32, i32, vp]
+        L.pat_unet_wgrad_scratch.argtypes = [i32, i32, i32, i32, i32]
+        L.pat_unet_wgrad_scratch.restype = i64
+        L.pat_unet_conv3_wgrad.argtypes = [vp, i32, i32, vp, i32, i32, i32, i32, i32, vp, vp, vp]
+        L.pat_unet_cast_weights.argtypes = [vp, i32, i32, vp, vp, vp]
+        L.pat_unet_relu_bwd.argtypes = [vp, i32, vp, i32, i32, i64, vp]
+        L.pat_unet_pool.argtypes = [vp, i32, i32, i32, i32, i32, vp, i32, vp]
+        L.pat_unet_pool_bwd_add.argtypes = [vp, i32, i32, i32, i32, i32, vp, i32, vp]
+        L.pat_unet_up.argtypes = [vp, i32, i32, i32, i32, i32, vp, i32, vp]
+        L.pat_unet_up_bwd.argtypes = [vp, i32, i32, i32, i32, i32, vp, i32, vp]
+        L.pat_unet_input.argtypes = [vp, f32, i64, vp, vp]
+        L.pat_unet_head.argtypes = [vp, vp, i64, vp, vp]
+        L.pat_unet_head_scratch.argtypes = [i64]
+        L.pat_unet_head_scratch.restype = i64
+        L.pat_unet_head_bwd.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp, vp, vp]
+        L.pat_unet_adam.argtypes = [vp, vp, vp, vp, i64, f32, f32, f32, f32, i32, vp]
+        for name in UNET_EXPORTS:
+            if name not in ("pat_unet_wgrad_scratch", "pat_unet_head_scratch"):
+                getattr(L, name).restype = ctypes.c_int
         L.pat_last_error.argtypes = []
         L.pat_last_error.restype = ctypes.c_char_p
         L.pat_version.argtypes = []

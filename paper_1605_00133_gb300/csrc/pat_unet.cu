@@ -1,0 +1,501 @@
+// pat_unet.cu - layers of the learned warm start (a 3D U-Net mapping A^T C^T f to a starting image
+// for the TV-Bregman solver): 3x3x3 convolutions on the tensor cores (BF16 operands, FP32
+// accumulation, mma.sync m16n8k16), their weight gradients, and the elementwise layers around them.
+//
+// Convolution as an implicit GEMM: M = voxels, N = output channels, K = 27 taps x input channels.
+// A CTA owns 128 consecutive voxels (8 warps x 16 rows) and BN output channels; each K step is one
+// tap and 16 input channels, staged in shared memory by cp.async (zero-filled where the tap falls
+// outside the volume) in a two-stage pipeline.  Shared rows are 24 BF16 (48 bytes): 16-byte aligned
+// for the copies and conflict-free for the fragment loads.
+//
+// Weight gradient: per tap t a GEMM with M = output channels, N = input channels and K = voxels,
+// split over voxel chunks (grid.x) and taps (grid.y); the chunk results go to a scratch buffer and
+// a second kernel sums them in a fixed order (deterministic).
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "../../include/pat_unet.h"
+#include "pat_internal.h"
+
+namespace {
+
+typedef __nv_bfloat16 bf16;
+
+constexpr int kBM = 128;     // voxels per convolution CTA
+constexpr int kPitch = 24;   // shared row pitch (BF16)
+constexpr int kChunk = 2048; // voxels per weight-gradient CTA
+
+__device__ __forceinline__ void mma16816(float* d, const uint32_t* a, const uint32_t* b) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+// 16-byte async copy; with valid = false nothing is read and the 16 bytes are zero-filled
+__device__ __forceinline__ void cp16z(void* smem, const void* gmem, bool valid) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    const int n = valid ? 16 : 0;
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(s), "l"(gmem), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+__device__ __forceinline__ uint32_t ld32(const bf16* p) { return *reinterpret_cast<const uint32_t*>(p); }
+
+template <int BN>
+__global__ void __launch_bounds__(256) conv3_fwd_kernel(const bf16* __restrict__ X, int ldx, int cin,
+                                                        const bf16* __restrict__ Wt, int cout,
+                                                        bf16* __restrict__ Y, int ldy, int D, int H, int W,
+                                                        int relu) {
+    __shared__ __align__(16) bf16 As[2][kBM * kPitch];
+    __shared__ __align__(16) bf16 Bs[2][BN * kPitch];
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, gid = lane >> 2, tig = lane & 3;
+    const int V = D * H * W;
+    const int v0 = blockIdx.x * kBM;
+    const int n0 = blockIdx.y * BN;
+    const int nc = cin / 16;
+    const int S = 27 * nc;
+    // copy role: voxel row am, channel half ah
+    const int am = tid >> 1, ah = tid & 1;
+    const int av = v0 + am;
+    const bool avalid = av < V;
+    int az = 0, ay = 0, ax = 0;
+    if (avalid) {
+        az = av / (H * W);
+        const int rr = av - az * H * W;
+        ay = rr / W;
+        ax = rr - ay * W;
+    }
+    auto issue = [&](int s, int buf) {
+        const int t = s / nc, c0 = (s - t * nc) * 16;
+        const int z = az + t / 9 - 1, y = ay + (t / 3) % 3 - 1, x = ax + t % 3 - 1;
+        const bool ok = avalid && z >= 0 && z < D && y >= 0 && y < H && x >= 0 && x < W;
+        const bf16* src = ok ? X + ((size_t)((z * H + y) * W + x) * ldx + c0 + ah * 8) : X;
+        cp16z(&As[buf][am * kPitch + ah * 8], src, ok);
+        for (int q = tid; q < 2 * BN; q += 256) {
+            const int n = q >> 1, hh = q & 1;
+            cp16z(&Bs[buf][n * kPitch + hh * 8], Wt + ((size_t)(t * cout + n0 + n) * cin + c0 + hh * 8), true);
+        }
+        cp_commit();
+    };
+    float acc[BN / 8][4];
+#pragma unroll
+    for (int i = 0; i < BN / 8; i++) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
+    issue(0, 0);
+    for (int s = 0; s < S; s++) {
+        if (s + 1 < S) {
+            issue(s + 1, (s + 1) & 1);
+            cp_wait<1>();
+        } else {
+            cp_wait<0>();
+        }
+        __syncthreads();
+        const bf16* A = As[s & 1] + warp * 16 * kPitch;
+        uint32_t a[4];
+        a[0] = ld32(A + gid * kPitch + 2 * tig);
+        a[1] = ld32(A + (gid + 8) * kPitch + 2 * tig);
+        a[2] = ld32(A + gid * kPitch + 2 * tig + 8);
+        a[3] = ld32(A + (gid + 8) * kPitch + 2 * tig + 8);
+        const bf16* Bb = Bs[s & 1];
+#pragma unroll
+        for (int nt = 0; nt < BN / 8; nt++) {
+            uint32_t b[2];
+            b[0] = ld32(Bb + (nt * 8 + gid) * kPitch + 2 * tig);
+            b[1] = ld32(Bb + (nt * 8 + gid) * kPitch + 2 * tig + 8);
+            mma16816(acc[nt], a, b);
+        }
+        __syncthreads();
+    }
+    const int r0 = v0 + warp * 16 + gid, r1 = r0 + 8;
+#pragma unroll
+    for (int nt = 0; nt < BN / 8; nt++) {
+        const int co = n0 + nt * 8 + 2 * tig;
+        float c0 = acc[nt][0], c1 = acc[nt][1], c2 = acc[nt][2], c3 = acc[nt][3];
+        if (relu) {
+            c0 = fmaxf(c0, 0.f);
+            c1 = fmaxf(c1, 0.f);
+            c2 = fmaxf(c2, 0.f);
+            c3 = fmaxf(c3, 0.f);
+        }
+        if (r0 < V) *reinterpret_cast<__nv_bfloat162*>(Y + (size_t)r0 * ldy + co) = __floats2bfloat162_rn(c0, c1);
+        if (r1 < V) *reinterpret_cast<__nv_bfloat162*>(Y + (size_t)r1 * ldy + co) = __floats2bfloat162_rn(c2, c3);
+    }
+}
+
+// partial[chunk][t][co][ci] = sum over the chunk's voxels v of dY[v][co] X[v + off_t][ci]
+constexpr int kWTiles = 16;  // mma tiles per warp (M/16 x N/8 <= 8 * 16)
+__global__ void __launch_bounds__(256) conv3_wgrad_kernel(const bf16* __restrict__ X, int ldx, int cin,
+                                                          const bf16* __restrict__ dY, int ldy, int cout,
+                                                          int D, int H, int W, float* __restrict__ partial) {
+    __shared__ __align__(16) bf16 At[128 * kPitch];  // [co][16 voxels]
+    __shared__ __align__(16) bf16 Bt[512 * kPitch];  // [ci][16 voxels]
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, gid = lane >> 2, tig = lane & 3;
+    const int V = D * H * W;
+    const int t = blockIdx.y;
+    const int oz = t / 9 - 1, oy = (t / 3) % 3 - 1, ox = t % 3 - 1;
+    const int vbeg = blockIdx.x * kChunk, vend = min(V, vbeg + kChunk);
+    const int NT8 = cin / 8, ntiles = (cout / 16) * NT8;
+    float acc[kWTiles][4];
+#pragma unroll
+    for (int i = 0; i < kWTiles; i++) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
+    for (int vb = vbeg; vb < vend; vb += 16) {
+        for (int e = tid; e < 16 * cout; e += 256) {
+            const int kk = e / cout, co = e - kk * cout;
+            const int v = vb + kk;
+            At[co * kPitch + kk] = (v < vend) ? dY[(size_t)v * ldy + co] : __float2bfloat16(0.f);
+        }
+        for (int e = tid; e < 16 * cin; e += 256) {
+            const int kk = e / cin, ci = e - kk * cin;
+            const int v = vb + kk;
+            bf16 val = __float2bfloat16(0.f);
+            if (v < vend) {
+                const int z = v / (H * W), rr = v - z * H * W, y = rr / W, x = rr - y * W;
+                const int zz = z + oz, yy = y + oy, xx = x + ox;
+                if (zz >= 0 && zz < D && yy >= 0 && yy < H && xx >= 0 && xx < W)
+                    val = X[(size_t)((zz * H + yy) * W + xx) * ldx + ci];
+            }
+            Bt[ci * kPitch + kk] = val;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int i = 0; i < kWTiles; i++) {
+            const int tile = warp + 8 * i;
+            if (tile < ntiles) {
+                const int mt = tile / NT8, nt = tile - mt * NT8;
+                const bf16* A = At + mt * 16 * kPitch;
+                uint32_t a[4], b[2];
+                a[0] = ld32(A + gid * kPitch + 2 * tig);
+                a[1] = ld32(A + (gid + 8) * kPitch + 2 * tig);
+                a[2] = ld32(A + gid * kPitch + 2 * tig + 8);
+                a[3] = ld32(A + (gid + 8) * kPitch + 2 * tig + 8);
+                const bf16* Bb = Bt + (nt * 8 + gid) * kPitch;
+                b[0] = ld32(Bb + 2 * tig);
+                b[1] = ld32(Bb + 2 * tig + 8);
+                mma16816(acc[i], a, b);
+            }
+        }
+        __syncthreads();
+    }
+    float* out = partial + ((size_t)blockIdx.x * 27 + t) * cout * cin;
+#pragma unroll
+    for (int i = 0; i < kWTiles; i++) {
+        const int tile = warp + 8 * i;
+        if (tile < ntiles) {
+            const int mt = tile / NT8, nt = tile - mt * NT8;
+            const int co = mt * 16 + gid, ci = nt * 8 + 2 * tig;
+            out[(size_t)co * cin + ci] = acc[i][0];
+            out[(size_t)co * cin + ci + 1] = acc[i][1];
+            out[(size_t)(co + 8) * cin + ci] = acc[i][2];
+            out[(size_t)(co + 8) * cin + ci + 1] = acc[i][3];
+        }
+    }
+}
+
+__global__ void sum_chunks_kernel(const float* __restrict__ partial, int nchunk, long long n, float* __restrict__ out) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        float s = 0.f;
+        for (int c = 0; c < nchunk; c++) s += partial[(size_t)c * n + i];
+        out[i] = s;
+    }
+}
+
+__global__ void cast_weights_kernel(const float* __restrict__ w32, int cin, int cout, bf16* __restrict__ wb,
+                                    bf16* __restrict__ wt) {
+    const int n = 27 * cin * cout;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int t = i / (cout * cin), r = i - t * cout * cin, co = r / cin, ci = r - co * cin;
+        const bf16 b = __float2bfloat16(w32[i]);
+        wb[i] = b;
+        wt[((size_t)(26 - t) * cin + ci) * cout + co] = b;
+    }
+}
+
+__global__ void relu_bwd_kernel(bf16* __restrict__ g, int ldg, const bf16* __restrict__ y, int ldy, int C, long long V) {
+    const long long n = V * C;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const long long v = i / C;
+        const int c = (int)(i - v * C);
+        if (!(__bfloat162float(y[v * ldy + c]) > 0.f)) g[v * ldg + c] = __float2bfloat16(0.f);
+    }
+}
+
+__global__ void pool_kernel(const bf16* __restrict__ x, int ldx, int C, int D, int H, int W, bf16* __restrict__ y, int ldy) {
+    const int D2 = D / 2, H2 = H / 2, W2 = W / 2;
+    const long long n = (long long)D2 * H2 * W2 * C;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        const long long p = i / C;
+        const int z = (int)(p / (H2 * W2)), r = (int)(p - (long long)z * H2 * W2), yy = r / W2, xx = r - yy * W2;
+        float s = 0.f;
+        for (int k = 0; k < 8; k++) {
+            const int cz = 2 * z + (k >> 2), cy = 2 * yy + ((k >> 1) & 1), cx = 2 * xx + (k & 1);
+            s += __bfloat162float(x[((size_t)(cz * H + cy) * W + cx) * ldx + c]);
+        }
+        y[p * ldy + c] = __float2bfloat16(0.125f * s);
+    }
+}
+
+__global__ void pool_bwd_add_kernel(const bf16* __restrict__ dy, int ldd, int C, int D, int H, int W, bf16* __restrict__ dx, int ldx) {
+    const long long n = (long long)D * H * W * C;
+    const int H2 = H / 2, W2 = W / 2;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        const long long v = i / C;
+        const int z = (int)(v / (H * W)), r = (int)(v - (long long)z * H * W), yy = r / W, xx = r - yy * W;
+        const long long pp = ((long long)(z / 2) * H2 + yy / 2) * W2 + xx / 2;
+        const float g = 0.125f * __bfloat162float(dy[pp * ldd + c]);
+        dx[v * ldx + c] = __float2bfloat16(__bfloat162float(dx[v * ldx + c]) + g);
+    }
+}
+
+__global__ void up_kernel(const bf16* __restrict__ x, int ldx, int C, int D, int H, int W, bf16* __restrict__ y, int ldy) {
+    const int D2 = 2 * D, H2 = 2 * H, W2 = 2 * W;
+    const long long n = (long long)D2 * H2 * W2 * C;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        const long long v = i / C;
+        const int z = (int)(v / (H2 * W2)), r = (int)(v - (long long)z * H2 * W2), yy = r / W2, xx = r - yy * W2;
+        y[v * ldy + c] = x[((size_t)((z / 2) * H + yy / 2) * W + xx / 2) * ldx + c];
+    }
+}
+
+__global__ void up_bwd_kernel(const bf16* __restrict__ dy, int ldd, int C, int D, int H, int W, bf16* __restrict__ dx, int ldx) {
+    const long long n = (long long)D * H * W * C;
+    const int H2 = 2 * H, W2 = 2 * W;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const int c = (int)(i % C);
+        const long long p = i / C;
+        const int z = (int)(p / (H * W)), r = (int)(p - (long long)z * H * W), yy = r / W, xx = r - yy * W;
+        float s = 0.f;
+        for (int k = 0; k < 8; k++) {
+            const int cz = 2 * z + (k >> 2), cy = 2 * yy + ((k >> 1) & 1), cx = 2 * xx + (k & 1);
+            s += __bfloat162float(dy[((size_t)(cz * H2 + cy) * W2 + cx) * ldd + c]);
+        }
+        dx[p * ldx + c] = __float2bfloat16(s);
+    }
+}
+
+__global__ void input_kernel(const float* __restrict__ xin, float s, long long V, bf16* __restrict__ x16) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < V * 16; i += (long long)gridDim.x * blockDim.x) {
+        const long long v = i >> 4;
+        x16[i] = __float2bfloat16((i & 15) == 0 ? s * xin[v] : 0.f);
+    }
+}
+
+__global__ void head_kernel(const bf16* __restrict__ h, const float* __restrict__ head, long long V, float* __restrict__ out) {
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
+        float s = head[16];
+#pragma unroll
+        for (int c = 0; c < 16; c++) s = fmaf(head[c], __bfloat162float(h[v * 16 + c]), s);
+        out[v] = s;
+    }
+}
+
+constexpr int kHeadBlocks = 256;
+// per block: 16 channel sums of g h, the sum of g, the sum of squared errors (fixed-order tree)
+__global__ void __launch_bounds__(256) head_bwd_kernel(const bf16* __restrict__ h, const float* __restrict__ head,
+                                                       const float* __restrict__ out, const float* __restrict__ target,
+                                                       long long V, bf16* __restrict__ dh, double* __restrict__ partial) {
+    __shared__ double red[256][18];
+    double acc[18];
+    for (int k = 0; k < 18; k++) acc[k] = 0.0;
+    const double gs = 2.0 / (double)V;
+    for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < V; v += (long long)gridDim.x * blockDim.x) {
+        const double e = (double)out[v] - (double)target[v];
+        const float g = (float)(gs * e);
+#pragma unroll
+        for (int c = 0; c < 16; c++) {
+            const float hv = __bfloat162float(h[v * 16 + c]);
+            acc[c] += (double)g * hv;
+            dh[v * 16 + c] = __float2bfloat16(g * head[c]);
+        }
+        acc[16] += g;
+        acc[17] += e * e;
+    }
+    for (int k = 0; k < 18; k++) red[threadIdx.x][k] = acc[k];
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+            for (int k = 0; k < 18; k++) red[threadIdx.x][k] += red[threadIdx.x + w][k];
+        __syncthreads();
+    }
+    if (threadIdx.x < 18) partial[(size_t)blockIdx.x * 18 + threadIdx.x] = red[0][threadIdx.x];
+}
+
+__global__ void head_bwd_final_kernel(const double* __restrict__ partial, int nb, long long V, float* __restrict__ ghead,
+                                      double* __restrict__ loss) {
+    const int k = threadIdx.x;
+    if (k >= 18) return;
+    double s = 0.0;
+    for (int b = 0; b < nb; b++) s += partial[(size_t)b * 18 + k];
+    if (k < 17) ghead[k] = (float)s;
+    else loss[0] = s / (double)V;
+}
+
+__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m, float* __restrict__ v,
+                            long long n, float lr, float b1, float b2, float eps, float c1, float c2) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+unsigned grid_for(long long n, int nt = 256) {
+    const long long b = (n + nt - 1) / nt;
+    return (unsigned)std::max(1LL, std::min(b, 152LL * 16));
+}
+
+bool al16(const void* p) { return ((uintptr_t)p & 15) == 0; }
+
+pat_status bad(const char* msg) { return pat::set_error(PAT_ERR_INVALID_ARG, msg); }
+
+pat_status launched(const char* where) {
+    const cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? PAT_OK : pat::set_cuda_error(e, where);
+}
+
+}  // namespace
+
+extern "C" {
+
+pat_status pat_unet_conv3(const void* x, int32_t ldx, int32_t cin, const void* w, int32_t cout, void* y,
+                          int32_t ldy, int32_t D, int32_t H, int32_t W, int32_t relu, void* stream) {
+    if (!x || !w || !y) return bad("pat_unet_conv3: NULL pointer");
+    if (cin < 16 || cin > 512 || cin % 16 || ldx < cin || ldx % 16 || ldy < cout || ldy % 16)
+        return bad("pat_unet_conv3: channel counts and strides must be multiples of 16 (cin <= 512)");
+    if (cout < 16 || cout > 1024 || cout % 16) return bad("pat_unet_conv3: cout must be a multiple of 16 (<= 1024)");
+    if (D < 1 || H < 1 || W < 1 || (int64_t)D * H * W > (1LL << 30)) return bad("pat_unet_conv3: bad volume");
+    if (!al16(x) || !al16(w) || !al16(y)) return bad("pat_unet_conv3: pointers must be 16-byte aligned");
+    const int V = D * H * W;
+    const cudaStream_t st = (cudaStream_t)stream;
+    const bf16* X = (const bf16*)x;
+    const bf16* Wt = (const bf16*)w;
+    bf16* Y = (bf16*)y;
+    const unsigned gx = (unsigned)((V + kBM - 1) / kBM);
+    // output-channel tile: the largest of 128, 64, 32, 16 that divides cout
+    if (cout % 128 == 0)
+        conv3_fwd_kernel<128><<<dim3(gx, cout / 128), 256, 0, st>>>(X, ldx, cin, Wt, cout, Y, ldy, D, H, W, relu);
+    else if (cout % 64 == 0)
+        conv3_fwd_kernel<64><<<dim3(gx, cout / 64), 256, 0, st>>>(X, ldx, cin, Wt, cout, Y, ldy, D, H, W, relu);
+    else if (cout % 32 == 0)
+        conv3_fwd_kernel<32><<<dim3(gx, cout / 32), 256, 0, st>>>(X, ldx, cin, Wt, cout, Y, ldy, D, H, W, relu);
+    else
+        conv3_fwd_kernel<16><<<dim3(gx, cout / 16), 256, 0, st>>>(X, ldx, cin, Wt, cout, Y, ldy, D, H, W, relu);
+    return launched("pat_unet_conv3");
+}
+
+int64_t pat_unet_wgrad_scratch(int32_t cin, int32_t cout, int32_t D, int32_t H, int32_t W) {
+    const int64_t V = (int64_t)D * H * W;
+    const int64_t nchunk = (V + kChunk - 1) / kChunk;
+    return nchunk * 27 * (int64_t)cin * cout;
+}
+
+pat_status pat_unet_conv3_wgrad(const void* x, int32_t ldx, int32_t cin, const void* dy, int32_t ldy, int32_t cout,
+                                int32_t D, int32_t H, int32_t W, float* partial, float* dw, void* stream) {
+    if (!x || !dy || !partial || !dw) return bad("pat_unet_conv3_wgrad: NULL pointer");
+    if (cin < 16 || cin > 512 || cin % 16 || ldx < cin || ldy < cout || cout < 16 || cout > 128 || cout % 16)
+        return bad("pat_unet_conv3_wgrad: cin in 16..512 and cout in 16..128, multiples of 16");
+    if ((cout / 16) * (cin / 8) > 8 * kWTiles) return bad("pat_unet_conv3_wgrad: cin * cout too large");
+    if (D < 1 || H < 1 || W < 1 || (int64_t)D * H * W > (1LL << 30)) return bad("pat_unet_conv3_wgrad: bad volume");
+    const int V = D * H * W;
+    const int nchunk = (V + kChunk - 1) / kChunk;
+    const cudaStream_t st = (cudaStream_t)stream;
+    conv3_wgrad_kernel<<<dim3(nchunk, 27), 256, 0, st>>>((const bf16*)x, ldx, cin, (const bf16*)dy, ldy, cout, D, H, W,
+                                                         partial);
+    const long long n = 27LL * cin * cout;
+    sum_chunks_kernel<<<grid_for(n), 256, 0, st>>>(partial, nchunk, n, dw);
+    return launched("pat_unet_conv3_wgrad");
+}
+
+pat_status pat_unet_cast_weights(const float* w32, int32_t cin, int32_t cout, void* wb, void* wt, void* stream) {
+    if (!w32 || !wb || !wt || cin < 1 || cout < 1) return bad("pat_unet_cast_weights: bad argument");
+    const long long n = 27LL * cin * cout;
+    cast_weights_kernel<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(w32, cin, cout, (bf16*)wb, (bf16*)wt);
+    return launched("pat_unet_cast_weights");
+}
+
+pat_status pat_unet_relu_bwd(void* g, int32_t ldg, const void* y, int32_t ldy, int32_t C, int64_t V, void* stream) {
+    if (!g || !y || C < 1 || ldg < C || ldy < C || V < 0) return bad("pat_unet_relu_bwd: bad argument");
+    relu_bwd_kernel<<<grid_for(V * C), 256, 0, (cudaStream_t)stream>>>((bf16*)g, ldg, (const bf16*)y, ldy, C, V);
+    return launched("pat_unet_relu_bwd");
+}
+
+pat_status pat_unet_pool(const void* x, int32_t ldx, int32_t C, int32_t D, int32_t H, int32_t W, void* y, int32_t ldy,
+                         void* stream) {
+    if (!x || !y || C < 1 || ldx < C || ldy < C || D < 2 || H < 2 || W < 2 || (D | H | W) & 1)
+        return bad("pat_unet_pool: bad argument (even dims >= 2)");
+    pool_kernel<<<grid_for((long long)D * H * W / 8 * C), 256, 0, (cudaStream_t)stream>>>((const bf16*)x, ldx, C, D, H, W,
+                                                                                       (bf16*)y, ldy);
+    return launched("pat_unet_pool");
+}
+
+pat_status pat_unet_pool_bwd_add(const void* dy, int32_t ldd, int32_t C, int32_t D, int32_t H, int32_t W, void* dx,
+                                 int32_t ldx, void* stream) {
+    if (!dy || !dx || C < 1 || ldx < C || ldd < C || D < 2 || H < 2 || W < 2 || (D | H | W) & 1)
+        return bad("pat_unet_pool_bwd_add: bad argument (even dims >= 2)");
+    pool_bwd_add_kernel<<<grid_for((long long)D * H * W * C), 256, 0, (cudaStream_t)stream>>>(
+        (const bf16*)dy, ldd, C, D, H, W, (bf16*)dx, ldx);
+    return launched("pat_unet_pool_bwd_add");
+}
+
+pat_status pat_unet_up(const void* x, int32_t ldx, int32_t C, int32_t D, int32_t H, int32_t W, void* y, int32_t ldy,
+                       void* stream) {
+    if (!x || !y || C < 1 || ldx < C || ldy < C || D < 1 || H < 1 || W < 1) return bad("pat_unet_up: bad argument");
+    up_kernel<<<grid_for(8LL * D * H * W * C), 256, 0, (cudaStream_t)stream>>>((const bf16*)x, ldx, C, D, H, W, (bf16*)y,
+                                                                              ldy);
+    return launched("pat_unet_up");
+}
+
+pat_status pat_unet_up_bwd(const void* dy, int32_t ldd, int32_t C, int32_t D, int32_t H, int32_t W, void* dx, int32_t ldx,
+                           void* stream) {
+    if (!dy || !dx || C < 1 || ldx < C || ldd < C || D < 1 || H < 1 || W < 1) return bad("pat_unet_up_bwd: bad argument");
+    up_bwd_kernel<<<grid_for((long long)D * H * W * C), 256, 0, (cudaStream_t)stream>>>((const bf16*)dy, ldd, C, D, H, W,
+                                                                                       (bf16*)dx, ldx);
+    return launched("pat_unet_up_bwd");
+}
+
+pat_status pat_unet_input(const float* xin, float s, int64_t V, void* x16, void* stream) {
+    if (!xin || !x16 || V < 0) return bad("pat_unet_input: bad argument");
+    input_kernel<<<grid_for(V * 16), 256, 0, (cudaStream_t)stream>>>(xin, s, V, (bf16*)x16);
+    return launched("pat_unet_input");
+}
+
+pat_status pat_unet_head(const void* h, const float* head, int64_t V, float* out, void* stream) {
+    if (!h || !head || !out || V < 0) return bad("pat_unet_head: bad argument");
+    head_kernel<<<grid_for(V), 256, 0, (cudaStream_t)stream>>>((const bf16*)h, head, V, out);
+    return launched("pat_unet_head");
+}
+
+int64_t pat_unet_head_scratch(int64_t V) {
+    (void)V;
+    return (int64_t)kHeadBlocks * 18;
+}
+
+pat_status pat_unet_head_bwd(const void* h, const float* head, const float* out, const float* target, int64_t V, void* dh,
+                             float* ghead, double* loss, double* partial, void* stream) {
+    if (!h || !head || !out || !target || !dh || !ghead || !loss || !partial || V < 1)
+        return bad("pat_unet_head_bwd: bad argument");
+    const cudaStream_t st = (cudaStream_t)stream;
+    head_bwd_kernel<<<kHeadBlocks, 256, 0, st>>>((const bf16*)h, head, out, target, V, (bf16*)dh, partial);
+    head_bwd_final_kernel<<<1, 32, 0, st>>>(partial, kHeadBlocks, V, ghead, loss);
+    return launched("pat_unet_head_bwd");
+}
+
+pat_status pat_unet_adam(float* p, const float* g, float* m, float* v, int64_t n, float lr, float b1, float b2, float eps,
+                         int32_t step, void* stream) {
+    if (!p || !g || !m || !v || n < 0 || step < 1) return bad("pat_unet_adam: bad argument");
+    const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
+    adam_kernel<<<grid_for(n), 256, 0, (cudaStream_t)stream>>>(p, g, m, v, n, lr, b1, b2, eps, c1, c2);
+    return launched("pat_unet_adam");
+}
+
+}  // extern "C"

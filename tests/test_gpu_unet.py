@@ -1,0 +1,193 @@
+"""Learned warm start on the GPU: every U-Net layer kernel and the whole network's forward pass and
+gradients against the FP64 reference (oracle/unet.py), and training that lowers the loss.
+
+Tolerances: BF16 operands (8-bit significands, relative rounding 2^-9) with FP32 accumulation.  A
+single layer whose inputs are exactly BF16 differs from FP64 only by the FP32 accumulation (weight
+gradients, FP32 output: 1e-5) or by the final rounding to BF16 (activations: 4e-3).  The whole
+network rounds activations at every one of its 14 convolutions: output 3e-2 (relative L2); its
+weight gradients, which pass through up to ten more roundings, 1e-1 with cosine > 0.99.
+
+Device tensors handed to a kernel are kept in variables until it has run: a temporary freed at once
+would hand its memory to the next allocation of the same size before the kernel reads it."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    return torch.device("cuda", 0)
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def bf16_exact(shape, seed, scale=1.0):
+    g = torch.Generator().manual_seed(seed)
+    return (torch.randn(shape, generator=g) * scale).to(torch.bfloat16).double()
+
+
+def to_dev_cl(x):
+    """[C][D][H][W] (double) -> channels-last BF16 [V][C] on the GPU"""
+    C = x.shape[0]
+    return x.permute(1, 2, 3, 0).reshape(-1, C).to(torch.bfloat16).cuda().contiguous()
+
+
+def from_dev_cl(y, C, D, H, W):
+    return y.double().cpu().reshape(D, H, W, -1)[..., :C].permute(3, 0, 1, 2)
+
+
+@pytest.mark.parametrize("cin,cout,dims", [(16, 16, (8, 8, 8)), (48, 16, (4, 8, 16)), (16, 48, (8, 4, 8)),
+                                           (192, 64, (4, 4, 4)), (64, 192, (2, 4, 2)), (128, 128, (2, 2, 2)),
+                                           (96, 32, (8, 8, 4)), (32, 96, (4, 8, 8))])
+def test_conv3_forward_and_data_gradient(dev, cin, cout, dims):
+    from oracle import unet as ou
+    from paper_1605_00133_gb300 import _lib
+    L = _lib.load()
+    D, H, W = dims
+    x = bf16_exact((cin, D, H, W), 1)
+    w32 = (torch.randn((27, cout, cin), generator=torch.Generator().manual_seed(2)) / (27 * cin) ** 0.5).float()
+    wq = w32.to(torch.bfloat16).double()
+    w32d = w32.cuda()
+    y_ref = ou.conv3(x, wq)
+    xd = to_dev_cl(x)
+    wb = torch.empty((27, cout, cin), dtype=torch.bfloat16, device=dev)
+    wt = torch.empty((27, cin, cout), dtype=torch.bfloat16, device=dev)
+    st = torch.cuda.current_stream().cuda_stream
+    _lib.check(L.pat_unet_cast_weights(w32d.data_ptr(), cin, cout, wb.data_ptr(), wt.data_ptr(), st))
+    yd = torch.zeros((D * H * W, cout), dtype=torch.bfloat16, device=dev)
+    _lib.check(L.pat_unet_conv3(xd.data_ptr(), cin, cin, wb.data_ptr(), cout, yd.data_ptr(), cout, D, H, W, 0, st))
+    torch.cuda.synchronize()
+    assert rel(from_dev_cl(yd, cout, D, H, W), y_ref) < 4e-3
+    # ReLU variant
+    _lib.check(L.pat_unet_conv3(xd.data_ptr(), cin, cin, wb.data_ptr(), cout, yd.data_ptr(), cout, D, H, W, 1, st))
+    torch.cuda.synchronize()
+    assert rel(from_dev_cl(yd, cout, D, H, W), torch.relu(y_ref)) < 4e-3
+    # gradient with respect to x through the transposed weights: conv3(dy, wt)
+    dy = bf16_exact((cout, D, H, W), 3)
+    xr = x.clone().requires_grad_(True)
+    (ou.conv3(xr, wq) * dy).sum().backward()
+    dxd = torch.zeros((D * H * W, cin), dtype=torch.bfloat16, device=dev)
+    dyd = to_dev_cl(dy)
+    _lib.check(L.pat_unet_conv3(dyd.data_ptr(), cout, cout, wt.data_ptr(), cin, dxd.data_ptr(), cin,
+                                D, H, W, 0, st))
+    torch.cuda.synchronize()
+    assert rel(from_dev_cl(dxd, cin, D, H, W), xr.grad) < 4e-3
+
+
+@pytest.mark.parametrize("cin,cout,dims", [(16, 16, (16, 16, 16)), (192, 64, (4, 8, 8)), (64, 128, (2, 4, 4)),
+                                           (48, 16, (8, 8, 40))])
+def test_conv3_weight_gradient(dev, cin, cout, dims):
+    from oracle import unet as ou
+    from paper_1605_00133_gb300 import _lib
+    L = _lib.load()
+    D, H, W = dims
+    x = bf16_exact((cin, D, H, W), 4)
+    dy = bf16_exact((cout, D, H, W), 5)
+    w = torch.zeros((27, cout, cin), dtype=torch.float64, requires_grad=True)
+    (ou.conv3(x, w) * dy).sum().backward()
+    st = torch.cuda.current_stream().cuda_stream
+    scratch = torch.empty(L.pat_unet_wgrad_scratch(cin, cout, D, H, W), dtype=torch.float32, device=dev)
+    dw = torch.empty((27, cout, cin), dtype=torch.float32, device=dev)
+    xd, dyd = to_dev_cl(x), to_dev_cl(dy)
+    _lib.check(L.pat_unet_conv3_wgrad(xd.data_ptr(), cin, cin, dyd.data_ptr(), cout, cout,
+                                      D, H, W, scratch.data_ptr(), dw.data_ptr(), st))
+    torch.cuda.synchronize()
+    assert rel(dw.cpu(), w.grad) < 1e-5
+
+
+def test_pool_up_and_their_backwards(dev):
+    from oracle import unet as ou
+    from paper_1605_00133_gb300 import _lib
+    L = _lib.load()
+    st = torch.cuda.current_stream().cuda_stream
+    C, D, H, W = 32, 4, 8, 6
+    x = bf16_exact((C, D, H, W), 6)
+    # pool into channel slice 16..48 of a 64-channel buffer
+    y = torch.zeros(((D // 2) * (H // 2) * (W // 2), 64), dtype=torch.bfloat16, device=dev)
+    xd = to_dev_cl(x)
+    _lib.check(L.pat_unet_pool(xd.data_ptr(), C, C, D, H, W, y.data_ptr() + 2 * 16, 64, st))
+    torch.cuda.synchronize()
+    yp = y.double().cpu().reshape(D // 2, H // 2, W // 2, 64)[..., 16:48].permute(3, 0, 1, 2)
+    assert rel(yp, ou.pool(x)) < 4e-3
+    u = torch.zeros((8 * D * H * W, C), dtype=torch.bfloat16, device=dev)
+    _lib.check(L.pat_unet_up(xd.data_ptr(), C, C, D, H, W, u.data_ptr(), C, st))
+    torch.cuda.synchronize()
+    assert torch.equal(from_dev_cl(u, C, 2 * D, 2 * H, 2 * W), ou.up(x))
+    g = bf16_exact((C, 2 * D, 2 * H, 2 * W), 7)
+    xr = x.clone().requires_grad_(True)
+    (ou.up(xr) * g).sum().backward()
+    dx = torch.zeros((D * H * W, C), dtype=torch.bfloat16, device=dev)
+    gd = to_dev_cl(g)
+    _lib.check(L.pat_unet_up_bwd(gd.data_ptr(), C, C, D, H, W, dx.data_ptr(), C, st))
+    torch.cuda.synchronize()
+    assert rel(from_dev_cl(dx, C, D, H, W), xr.grad) < 4e-3
+    # pool backward accumulates into an existing gradient
+    base = bf16_exact((C, D, H, W), 8)
+    gp = bf16_exact((C, D // 2, H // 2, W // 2), 9)
+    xr = x.clone().requires_grad_(True)
+    (ou.pool(xr) * gp).sum().backward()
+    acc = to_dev_cl(base)
+    gpd = to_dev_cl(gp)
+    _lib.check(L.pat_unet_pool_bwd_add(gpd.data_ptr(), C, C, D, H, W, acc.data_ptr(), C, st))
+    torch.cuda.synchronize()
+    assert rel(from_dev_cl(acc, C, D, H, W), base + xr.grad) < 4e-3
+
+
+def _net_and_ref(dev, D, H, W, seed):
+    from oracle import unet as ou
+    from paper_1605_00133_gb300 import unet as un
+    params = un.init_params(seed)
+    # weights rounded to BF16 on both sides, so the comparison sees activation rounding only
+    params = {k: (v.to(torch.bfloat16).float() if k != "head" else v) for k, v in params.items()}
+    net = un.WarmStartUNet(D, H, W, seed=seed, params=params)
+    g = torch.Generator().manual_seed(seed + 1)
+    xin = torch.rand((D, H, W), generator=g, dtype=torch.float64)
+    target = torch.rand((D, H, W), generator=g, dtype=torch.float64)
+    return ou, net, params, xin, target
+
+
+def test_network_forward_and_gradients_match_the_reference(dev):
+    # 32^3: the deepest level still has 4^3 voxels, so its weight gradients are not short sums
+    # dominated by a few rounding-flipped ReLU masks
+    ou, net, params, xin, target = _net_and_ref(dev, 32, 32, 32, 5)
+    loss_ref, out_ref, g_ref = ou.loss_and_grads(params, xin, target, 1.0)
+    xs, ts = xin.float().cuda(), target.float().cuda()
+    out = net.forward(xs)
+    loss = net.backward(ts)
+    torch.cuda.synchronize()
+    assert rel(out.double().cpu().reshape(32, 32, 32), out_ref) < 3e-2
+    assert abs(float(loss) - loss_ref) < 3e-2 * loss_ref
+    # each backward kernel is held to its own bound above; through ~10 BF16 roundings of the
+    # back-propagated signal (and ReLU masks flipping where a pre-activation rounds across zero) the
+    # deepest weight gradients drift a few per cent, while a wiring error (a wrong buffer, channel
+    # offset or order) gives errors near 100 %
+    grads = net.grads()
+    errs = {}
+    for name, gr in g_ref.items():
+        a = grads[name].double().reshape(-1)
+        b = gr.reshape(-1)
+        errs[name] = rel(a, b)
+        assert errs[name] < 0.1, (name, errs)
+        assert float(a @ b / (a.norm() * b.norm())) > 0.99, (name, errs)
+
+
+def test_training_lowers_the_loss(dev):
+    ou, net, params, xin, target = _net_and_ref(dev, 16, 16, 16, 7)
+    xs = xin.float().cuda()
+    # a target the network can represent: the input itself (through the skip connections)
+    tgt = xin.float().cuda()
+    losses = []
+    for _ in range(60):
+        losses.append(float(net.train_step(xs, tgt, lr=3e-3)))
+    assert losses[-1] < 0.2 * losses[0], losses[::10]

@@ -18,10 +18,10 @@ def lib():
     return _lib.load()
 
 
-def declared_functions():
-    src = open(os.path.join(ROOT, "include", "pat.h")).read()
+def declared_functions(header="pat.h"):
+    src = open(os.path.join(ROOT, "include", header)).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"\b(pat_[a-z_]+)\s*\(", src)))
+    return sorted(set(re.findall(r"\b(pat_[a-z0-9_]+)\s*\(", src)))
 
 
 def test_header_declares_the_boundary():
@@ -37,6 +37,11 @@ def test_every_declared_symbol_is_exported(lib):
     for n in names:
         assert hasattr(lib, n), n
     assert lib.pat_version().startswith(b"libpat")
+    unet = declared_functions("pat_unet.h")
+    assert sorted(_lib.UNET_EXPORTS) == unet
+    for n in unet:
+        assert hasattr(lib, n), n
+    assert sorted(os.listdir(os.path.join(ROOT, "include"))) == ["pat.h", "pat_unet.h"]
 
 
 def _desc(**kw):

@@ -47,6 +47,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--solve", action="store_true",
                     help="also time one TV-Bregman reconstruction of the workload (reported, not the metric)")
+    ap.add_argument("--warm", action="store_true",
+                    help="also train the learned warm start and time warm vs plain solves to 2 %% error")
+    ap.add_argument("--warm-train", type=int, default=64)
+    ap.add_argument("--warm-test", type=int, default=4)
+    ap.add_argument("--warm-epochs", type=int, default=20)
     return ap.parse_args()
 
 
@@ -353,6 +358,10 @@ def main():
                  "warm_seconds_to_2pct": None,
                  "warm_start": "not built (learned U-Net warm start); the plain cold-start solve is timed"}
 
+    warm = None
+    if args.warm and B == 1:
+        warm = warm_start_experiment(args, op, g, dev)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         Ts = 100
@@ -370,11 +379,58 @@ def main():
                 "roofline": roofline, "roofline_alu": roofline_alu, "kernels": kernels, "cpu_baseline": cpu}
         if solve is not None:
             line["solve"] = solve
+        if warm is not None:
+            line["warm_start"] = warm
         print(json.dumps(line), flush=True)
     op.close()
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def warm_start_experiment(args, op, g, dev):
+    """Train the U-Net warm start on seeded phantoms of the workload and compare warm vs plain solves
+    on held-out phantoms (time to 2 % relative error against the plain solve's final image)."""
+    import numpy as np
+    import torch
+
+    from paper_1605_00133_gb300 import presets, unet, warmstart
+    wl = presets.workload(args.workload)
+    lam = 2e-4
+    # the step size 1/L (power iteration) once per grid, shared by every solve below
+    _, rep = op.bregman_solve(torch.zeros(op.data_shape, device=dev), lam, outer=1, inner=1, prox_iters=1,
+                              power_iters=20)
+    L = rep["L"]
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    train_pairs = warmstart.make_pairs(op, wl, args.warm_train, 1000, lam, wl.bregman_outer, wl.inner, L)
+    test_pairs = warmstart.make_pairs(op, wl, args.warm_test, 5000, lam, wl.bregman_outer, wl.inner, L)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    net = unet.WarmStartUNet(g.nz, g.ny, g.nx, seed=0)
+    net.s_in = warmstart.input_scale(train_pairs)
+    t0 = time.perf_counter()
+    hist = warmstart.train(net, train_pairs, args.warm_epochs, lr=1e-3, seed=0)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    steps = args.warm_epochs * len(train_pairs)
+    inners = [10, 20, 30, 40, wl.inner]
+    ev = warmstart.evaluate(op, net, test_pairs, lam, wl.bregman_outer, inners, L)
+    t_plain = [e["plain_seconds_to_tol"] for e in ev]
+    t_warm = [e["warm_seconds_to_tol"] for e in ev]
+
+    def med(v):
+        v = [x for x in v if x is not None]
+        return float(np.median(v)) if v else None
+    return {"train_pairs": len(train_pairs), "test_pairs": len(test_pairs), "epochs": args.warm_epochs,
+            "train_steps": steps, "train_seconds": t_train, "train_ms_per_step": 1e3 * t_train / steps,
+            "data_seconds": t_data, "loss_per_epoch": hist, "L": L, "lambda": lam,
+            "schedule": {"outer": wl.bregman_outer, "inner": inners, "tol": 0.02},
+            "network_rel_err": [e["network_rel_err"] for e in ev],
+            "inference_seconds": [e["inference_seconds"] for e in ev],
+            "plain_seconds_to_2pct": t_plain, "warm_seconds_to_2pct": t_warm,
+            "median_plain_seconds_to_2pct": med(t_plain), "median_warm_seconds_to_2pct": med(t_warm),
+            "trajectories": [{"plain": e["plain"], "warm": e["warm"]} for e in ev]}
 
 
 def _source_hash():

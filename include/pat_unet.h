@@ -34,7 +34,7 @@ pat_status pat_unet_conv3(const void* x, int32_t ldx, int32_t cin, const void* w
 
 /* Weight gradient of pat_unet_conv3: dw[t][co][ci] = sum_v dy[v][co] x[v + off_t][ci] (FP32,
  * overwritten), dy the gradient at the convolution's output (after the activation's backward);
- * cin in 16..512, cout in 16..128 (multiples of 16), (cout/16) (cin/8) <= 128.
+ * cin in 16..256, cout in 16..128 (multiples of 16), (cout/16) (cin/8) <= 128.
  * partial: FP32 scratch of at least pat_unet_wgrad_scratch(...) floats; deterministic (fixed-order
  * two-stage reduction). */
 int64_t pat_unet_wgrad_scratch(int32_t cin, int32_t cout, int32_t D, int32_t H, int32_t W);

@@ -9,8 +9,9 @@
 // for the copies and conflict-free for the fragment loads.
 //
 // Weight gradient: per tap t a GEMM with M = output channels, N = input channels and K = voxels,
-// split over voxel chunks (grid.x) and taps (grid.y); the chunk results go to a scratch buffer and
-// a second kernel sums them in a fixed order (deterministic).
+// split over voxel chunks (grid.x) and taps (grid.y), both operands staged transposed in shared
+// memory 32 voxels at a time; the chunk results go to a scratch buffer and a second kernel sums them
+// in a fixed order (deterministic).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -128,55 +129,71 @@ __global__ void __launch_bounds__(256) conv3_fwd_kernel(const bf16* __restrict__
 }
 
 // partial[chunk][t][co][ci] = sum over the chunk's voxels v of dY[v][co] X[v + off_t][ci]
-constexpr int kWTiles = 16;  // mma tiles per warp (M/16 x N/8 <= 8 * 16)
+// Both operands are staged transposed ([channel][voxel], 32 voxels per stage, row pitch 40 BF16 =
+// 80 bytes: conflict-free fragment loads); a thread moves one 8-channel vector of one voxel (one
+// 16-byte load, one neighbour computation) and scatters it down a column, consecutive lanes taking
+// consecutive voxels, so each scattered store instruction covers 64 contiguous bytes.
+constexpr int kWTiles = 16;   // mma tiles per warp (M/16 x N/8 <= 8 * 16)
+constexpr int kWV = 32;       // voxels per stage
+constexpr int kWPitch = 40;   // staged row pitch (BF16)
 __global__ void __launch_bounds__(256) conv3_wgrad_kernel(const bf16* __restrict__ X, int ldx, int cin,
                                                           const bf16* __restrict__ dY, int ldy, int cout,
                                                           int D, int H, int W, float* __restrict__ partial) {
-    __shared__ __align__(16) bf16 At[128 * kPitch];  // [co][16 voxels]
-    __shared__ __align__(16) bf16 Bt[512 * kPitch];  // [ci][16 voxels]
+    __shared__ __align__(16) bf16 At[128 * kWPitch];  // [co][32 voxels]
+    __shared__ __align__(16) bf16 Bt[256 * kWPitch];  // [ci][32 voxels]
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, gid = lane >> 2, tig = lane & 3;
     const int V = D * H * W;
     const int t = blockIdx.y;
     const int oz = t / 9 - 1, oy = (t / 3) % 3 - 1, ox = t % 3 - 1;
     const int vbeg = blockIdx.x * kChunk, vend = min(V, vbeg + kChunk);
     const int NT8 = cin / 8, ntiles = (cout / 16) * NT8;
+    const int ncot = cout / 8, ncit = cin / 8;  // 8-channel vectors per voxel
     float acc[kWTiles][4];
 #pragma unroll
     for (int i = 0; i < kWTiles; i++) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
-    for (int vb = vbeg; vb < vend; vb += 16) {
-        for (int e = tid; e < 16 * cout; e += 256) {
-            const int kk = e / cout, co = e - kk * cout;
+    for (int vb = vbeg; vb < vend; vb += kWV) {
+        for (int q = tid; q < kWV * ncot; q += 256) {
+            const int kk = q % kWV, ch = q / kWV;
             const int v = vb + kk;
-            At[co * kPitch + kk] = (v < vend) ? dY[(size_t)v * ldy + co] : __float2bfloat16(0.f);
+            uint4 w = make_uint4(0, 0, 0, 0);
+            if (v < vend) w = *reinterpret_cast<const uint4*>(dY + (size_t)v * ldy + 8 * ch);
+            const bf16* e = reinterpret_cast<const bf16*>(&w);
+#pragma unroll
+            for (int j = 0; j < 8; j++) At[(8 * ch + j) * kWPitch + kk] = e[j];
         }
-        for (int e = tid; e < 16 * cin; e += 256) {
-            const int kk = e / cin, ci = e - kk * cin;
+        for (int q = tid; q < kWV * ncit; q += 256) {
+            const int kk = q % kWV, ch = q / kWV;
             const int v = vb + kk;
-            bf16 val = __float2bfloat16(0.f);
+            uint4 w = make_uint4(0, 0, 0, 0);
             if (v < vend) {
                 const int z = v / (H * W), rr = v - z * H * W, y = rr / W, x = rr - y * W;
                 const int zz = z + oz, yy = y + oy, xx = x + ox;
                 if (zz >= 0 && zz < D && yy >= 0 && yy < H && xx >= 0 && xx < W)
-                    val = X[(size_t)((zz * H + yy) * W + xx) * ldx + ci];
+                    w = *reinterpret_cast<const uint4*>(X + (size_t)((zz * H + yy) * W + xx) * ldx + 8 * ch);
             }
-            Bt[ci * kPitch + kk] = val;
+            const bf16* e = reinterpret_cast<const bf16*>(&w);
+#pragma unroll
+            for (int j = 0; j < 8; j++) Bt[(8 * ch + j) * kWPitch + kk] = e[j];
         }
         __syncthreads();
 #pragma unroll
-        for (int i = 0; i < kWTiles; i++) {
-            const int tile = warp + 8 * i;
-            if (tile < ntiles) {
-                const int mt = tile / NT8, nt = tile - mt * NT8;
-                const bf16* A = At + mt * 16 * kPitch;
-                uint32_t a[4], b[2];
-                a[0] = ld32(A + gid * kPitch + 2 * tig);
-                a[1] = ld32(A + (gid + 8) * kPitch + 2 * tig);
-                a[2] = ld32(A + gid * kPitch + 2 * tig + 8);
-                a[3] = ld32(A + (gid + 8) * kPitch + 2 * tig + 8);
-                const bf16* Bb = Bt + (nt * 8 + gid) * kPitch;
-                b[0] = ld32(Bb + 2 * tig);
-                b[1] = ld32(Bb + 2 * tig + 8);
-                mma16816(acc[i], a, b);
+        for (int k0 = 0; k0 < kWV; k0 += 16) {
+#pragma unroll
+            for (int i = 0; i < kWTiles; i++) {
+                const int tile = warp + 8 * i;
+                if (tile < ntiles) {
+                    const int mt = tile / NT8, nt = tile - mt * NT8;
+                    const bf16* A = At + mt * 16 * kWPitch + k0;
+                    uint32_t a[4], b[2];
+                    a[0] = ld32(A + gid * kWPitch + 2 * tig);
+                    a[1] = ld32(A + (gid + 8) * kWPitch + 2 * tig);
+                    a[2] = ld32(A + gid * kWPitch + 2 * tig + 8);
+                    a[3] = ld32(A + (gid + 8) * kWPitch + 2 * tig + 8);
+                    const bf16* Bb = Bt + (nt * 8 + gid) * kWPitch + k0;
+                    b[0] = ld32(Bb + 2 * tig);
+                    b[1] = ld32(Bb + 2 * tig + 8);
+                    mma16816(acc[i], a, b);
+                }
             }
         }
         __syncthreads();
@@ -402,8 +419,10 @@ int64_t pat_unet_wgrad_scratch(int32_t cin, int32_t cout, int32_t D, int32_t H, 
 pat_status pat_unet_conv3_wgrad(const void* x, int32_t ldx, int32_t cin, const void* dy, int32_t ldy, int32_t cout,
                                 int32_t D, int32_t H, int32_t W, float* partial, float* dw, void* stream) {
     if (!x || !dy || !partial || !dw) return bad("pat_unet_conv3_wgrad: NULL pointer");
-    if (cin < 16 || cin > 512 || cin % 16 || ldx < cin || ldy < cout || cout < 16 || cout > 128 || cout % 16)
-        return bad("pat_unet_conv3_wgrad: cin in 16..512 and cout in 16..128, multiples of 16");
+    if (cin < 16 || cin > 256 || cin % 16 || ldx < cin || ldx % 8 || ldy < cout || ldy % 8 || cout < 16 ||
+        cout > 128 || cout % 16)
+        return bad("pat_unet_conv3_wgrad: cin in 16..256 and cout in 16..128, multiples of 16");
+    if (!al16(x) || !al16(dy)) return bad("pat_unet_conv3_wgrad: pointers must be 16-byte aligned");
     if ((cout / 16) * (cin / 8) > 8 * kWTiles) return bad("pat_unet_conv3_wgrad: cin * cout too large");
     if (D < 1 || H < 1 || W < 1 || (int64_t)D * H * W > (1LL << 30)) return bad("pat_unet_conv3_wgrad: bad volume");
     const int V = D * H * W;

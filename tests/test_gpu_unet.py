@@ -86,7 +86,7 @@ def test_conv3_forward_and_data_gradient(dev, cin, cout, dims):
 
 
 @pytest.mark.parametrize("cin,cout,dims", [(16, 16, (16, 16, 16)), (192, 64, (4, 8, 8)), (64, 128, (2, 4, 4)),
-                                           (48, 16, (8, 8, 40))])
+                                           (48, 16, (8, 8, 40)), (32, 32, (3, 5, 7))])
 def test_conv3_weight_gradient(dev, cin, cout, dims):
     from oracle import unet as ou
     from paper_1605_00133_gb300 import _lib

@@ -199,7 +199,7 @@ def main():
         dist.barrier()
     __graft_entry__.build()
 
-    from paper_1605_00133_gb300 import presets
+    from paper_1605_00133_gb300 import presets, replicas
     from paper_1605_00133_gb300.operators import PatOperator
 
     w = presets.workload(args.workload)
@@ -208,7 +208,7 @@ def main():
     gb = presets.Grid(g.nz, g.ny, g.nx, dx=g.dx, c=g.c, rho0=g.rho0, cfl=g.cfl, T=g.T,
                       pml_size=g.pml_size, pml_alpha=g.pml_alpha, sensor_z=g.sensor_z, batch=B)
     op = PatOperator(gb, w.sampling)
-    p0_np = np.stack([w.p0(seed_offset=100 * rank + b) for b in range(B)]).astype(np.float32)
+    p0_np = np.stack([w.p0(seed_offset=o) for o in replicas.volume_seeds(rank, B)]).astype(np.float32)
     p0 = torch.tensor(p0_np, device=dev)
     f = torch.empty(op.data_shape, device=dev)
     p = torch.empty(op.image_shape, device=dev)
@@ -225,11 +225,7 @@ def main():
         torch.cuda.synchronize()
 
     def max_over_ranks(x):
-        if not dist:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return replicas.max_over_ranks(x, dist, dev)
 
     for _ in range(args.warmup):
         step()
@@ -247,7 +243,7 @@ def main():
     barrier()
     ms = max_over_ranks(ms)
     pairs = B * world * args.steps
-    value = pairs / (ms / 1e3)
+    value = replicas.whole_job_rate(B * args.steps, world, ms / 1e3)
 
     # per-kernel breakdown: the same K steps again with every launch bracketed by CUDA events on the
     # launching stream (torch's current stream, which the library uses)

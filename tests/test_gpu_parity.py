@@ -79,6 +79,18 @@ def test_adjoint_full_plane_matches_oracle(oracle_mod, dev, shape):
     assert rel(got, ref) < TOL
 
 
+@pytest.mark.parametrize("cfl", [0.55, 0.8])
+def test_large_time_steps_match_oracle(oracle_mod, dev, cfl):
+    """Larger time steps: the argument of kappa = sinc(c dt |k| / 2) reaches 1.5 at CFL 0.55 and 2.2
+    at CFL 0.8 (0.82 at the workloads' CFL 0.3)."""
+    g = presets.Grid(16, 32, 16, T=10, pml_size=3, cfl=cfl)
+    p0 = np.random.default_rng(7).standard_normal(g.shape)
+    op = make_op(g, full(g))
+    assert rel(gpu_forward(op, p0, dev), oracle_mod.forward_plane(g, p0)) < TOL
+    y = np.random.default_rng(8).standard_normal((g.T, g.m_plane))
+    assert rel(gpu_adjoint(op, y, dev), oracle_mod.adjoint_plane(g, y)) < TOL
+
+
 def test_workload_c1_forward_and_adjoint(oracle_mod, dev):
     """32^3, T = 64, 8-voxel PML, rSP 25 %, three Gaussian balls."""
     w = presets.workload("c1")

@@ -248,6 +248,29 @@ def branching_tubes(shape, n_tubes: int, seed: int, pml: int = 0, radius_range=(
 # Noise
 # --------------------------------------------------------------------------------------------
 
+def band_limit(vol: np.ndarray) -> np.ndarray:
+    """vol with its Nyquist planes removed (the field's spectrum then lies strictly inside the grid's
+    band, so it is represented identically on any finer grid)."""
+    F = np.fft.fftn(vol)
+    for ax, n in enumerate(vol.shape):
+        idx = [slice(None)] * vol.ndim
+        idx[ax] = n // 2
+        F[tuple(idx)] = 0.0
+    return np.fft.ifftn(F).real
+
+
+def upsample2(vol: np.ndarray) -> np.ndarray:
+    """The band-limited (trigonometric) interpolant of vol on the grid with half the spacing: equal to
+    vol at the coincident points [::2, ::2, ::2].  vol must have no Nyquist content (band_limit)."""
+    F = np.fft.fftn(vol)
+    shape2 = tuple(2 * n for n in vol.shape)
+    G = np.zeros(shape2, dtype=complex)
+    sl = [np.r_[0:n // 2, n * 2 - n // 2:n * 2] for n in vol.shape]
+    src = [np.r_[0:n // 2, n - n // 2:n] for n in vol.shape]
+    G[np.ix_(*sl)] = F[np.ix_(*src)]
+    return np.fft.ifftn(G).real * 8.0
+
+
 def gaussian_noise(shape, sigma: float, seed: int) -> np.ndarray:
     """i.i.d. N(0, sigma^2) noise of the given shape."""
     n = int(np.prod(shape))

@@ -297,6 +297,25 @@ def test_c4_grid_without_pml_matches_exact_solution(oracle_mod, dev):
     op.close()
 
 
+@pytest.mark.slow
+def test_c4_grid_agrees_with_oracle_on_2x_coarser_grid(oracle_mod, dev):
+    """The c4 grid (128x256x256, dx 50 um, dt 10 ns, T = 799) on the GPU against the FP64 oracle on
+    the 2x coarser c2-sized grid (64x128x128, dx 100 um, dt 20 ns, T = 400), PML off, for the c2 vessel
+    phantom band-limited to the coarse grid and interpolated to the fine one.  The k-space step is
+    exact per mode for any time step, and the fine grid carries exactly the coarse grid's modes, so
+    the fine sensor data at coincident points (even x, y) and times (even n) equal the coarse ones."""
+    pc = synth.band_limit(presets.workload("c2").p0())
+    pf = synth.upsample2(pc)
+    gc = presets.Grid(64, 128, 128, dx=100e-6, T=400, pml_size=0, sensor_z=0)
+    gf = presets.Grid(128, 256, 256, dx=50e-6, T=799, pml_size=0, sensor_z=0)
+    assert abs(gf.dt - gc.dt / 2) < 1e-20
+    op = make_op(gf, full(gf))
+    f = gpu_forward(op, pf, dev).reshape(gf.T, gf.ny, gf.nx)[::2, ::2, ::2]
+    op.close()
+    ref = oracle_mod.forward_plane(gc, pc).reshape(gc.T, gc.ny, gc.nx)
+    assert rel(f, ref) < TOL
+
+
 def test_c4_workload_forward_and_adjoint_match_oracle_reduced_T(oracle_mod, dev):
     """Full c4 grid and sampling (10-voxel PML, rSP 4096 of 65536), T = 6."""
     w = presets.shrink(presets.workload("c4"), 6)

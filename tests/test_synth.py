@@ -52,3 +52,16 @@ def test_noise_level():
     f = np.ones((100, 100))
     n = synth.add_relative_noise(f, 0.01, 5) - f
     assert abs(n.std() - 0.01) < 1e-3
+
+
+def test_band_limited_upsampling_keeps_the_coarse_values():
+    from paper_1605_00133_gb300 import synth
+    v = np.random.default_rng(3).standard_normal((8, 6, 10))
+    b = synth.band_limit(v)
+    assert np.abs(synth.band_limit(b) - b).max() < 1e-12
+    u = synth.upsample2(b)
+    assert u.shape == (16, 12, 20)
+    assert np.abs(u[::2, ::2, ::2] - b).max() < 1e-12
+    # the interpolant has no content above the coarse band
+    U = np.fft.fftn(u)
+    assert np.abs(U[4:12]).max() < 1e-9 * np.abs(U).max()

@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "pat_internal.h"
+#include "pat_kargs.h"
 
 using namespace pat;
 
@@ -161,6 +162,22 @@ pat_status build_tables(pat_grid* G) {
             tw[m] = make_float2((float)cos(ang), (float)sin(ang));
         }
         if ((st = upload(G, &G->t.tw[a], tw, "twiddles")) != PAT_OK) return st;
+        // per-thread tables of the line passes (layouts in pat_kargs.h, LineKernels)
+        const LineKernels lk = line_kernels_for(n[a]);
+        const int L = n[a], ra = lk.ra, rb = lk.rb;
+        if (ra * rb != L) return fail(PAT_ERR_INVALID_ARG, "no line kernel for this axis length");
+        std::vector<float2> twi(L), twf(L);
+        for (int k = 0; k < rb; k++)
+            for (int r = 0; r < ra; r++) twi[k * ra + r] = make_float2(tw[(r * k) % L].x, -tw[(r * k) % L].y);
+        if (lk.pair) {
+            for (int k = 0; k < rb; k++)
+                for (int r = 0; r < ra; r++) twf[k * ra + r] = tw[((r / 2) * (2 * k + r % 2)) % L];
+        } else {
+            for (int k = 0; k < ra; k++)
+                for (int r = 0; r < rb; r++) twf[k * rb + r] = tw[(r * k) % L];
+        }
+        if ((st = upload(G, &G->t.twi[a], twi, "twiddles")) != PAT_OK) return st;
+        if ((st = upload(G, &G->t.twf[a], twf, "twiddles")) != PAT_OK) return st;
     }
     // derivative factors, every bin of each axis
     for (int a = 0; a < 3; a++) {
@@ -177,11 +194,13 @@ pat_status build_tables(pat_grid* G) {
         if ((st = upload(G, &G->t.dplus[a], dp, "dplus")) != PAT_OK) return st;
         if ((st = upload(G, &G->t.dminus[a], dm, "dminus")) != PAT_OK) return st;
     }
-    // kappa at every line point of each axis, [len][ncols] in the line layout of pat_internal.h
+    // kappa at every line point of each axis, tile-major [ntile][len][tc] like the states
+    // (pat_internal.h); padding lines 0
     {
         const Geom& g = G->g;
         for (int a = 0; a < 3; a++) {
-            std::vector<float> kap((size_t)g.len[a] * g.ncols[a]);
+            const int tc = g.tc[a];
+            std::vector<float> kap((size_t)g.ntile[a] * g.len[a] * tc, 0.0f);
             for (int j = 0; j < g.len[a]; j++) {
                 for (int c = 0; c < g.ncols[a]; c++) {
                     int kz, ky, kx;
@@ -192,7 +211,7 @@ pat_status build_tables(pat_grid* G) {
                     const double wy = wavenumber(ky, d.ny, d.dx);
                     const double wx = wavenumber(kx, d.nx, d.dx);
                     const double x = 0.5 * d.c * dt * sqrt(wz * wz + wy * wy + wx * wx);
-                    kap[(size_t)j * g.ncols[a] + c] = (float)((x == 0.0) ? 1.0 : sin(x) / x);
+                    kap[((size_t)(c / tc) * g.len[a] + j) * tc + c % tc] = (float)((x == 0.0) ? 1.0 : sin(x) / x);
                 }
             }
             if ((st = upload(G, &G->t.kappa[a], kap, "kappa")) != PAT_OK) return st;
@@ -245,7 +264,7 @@ WsLayout workspace_layout(const Geom& g, int kind) {
     WsLayout L;
     size_t loop = 0;
     for (int a = 0; a < 3; a++) {
-        L.ms[a] = round256(B * (size_t)g.len[a] * g.ncols[a] * sizeof(float2));
+        L.ms[a] = round256(B * (size_t)g.len[a] * g.ntile[a] * g.tc[a] * sizeof(float2));
         loop += 2 * L.ms[a];
     }
     L.ph = round256(B * (size_t)g.nspec * sizeof(float2));
@@ -321,6 +340,11 @@ pat_status pat_create_grid(const pat_grid_desc* desc, const pat_sampling_desc* s
     g.ncols[AZ] = g.nxh * g.ny;
     g.ncols[AY] = g.nz * g.nxh;
     g.ncols[AX] = g.nzh * g.ny;
+    for (int a = 0; a < 3; a++) {
+        const int tc = line_kernels_for(g.len[a]).tc;
+        g.tc[a] = tc > 0 ? tc : 1;
+        g.ntile[a] = (g.ncols[a] + g.tc[a] - 1) / g.tc[a];
+    }
     g.nreal = (long long)g.nz * g.ny * g.nx;
     g.nspec = (long long)g.nz * g.ny * g.nxh;
     g.nplane = (long long)g.nxh * g.ny;

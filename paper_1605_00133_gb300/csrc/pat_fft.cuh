@@ -15,8 +15,12 @@
 
 namespace pat {
 
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// Complex addition and subtraction as one packed FP32x2 instruction each (two IEEE single-precision
+// operations, round to nearest: the same values as two scalar ones); a - b is fma(b, -1, a), exact.
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+// s a + b with s = +-1 in both lanes (thread-pair butterflies: sum or difference by lane)
+__device__ __forceinline__ float2 csgn_add(float2 s, float2 a, float2 b) { return __ffma2_rn(s, a, b); }
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
@@ -50,16 +54,16 @@ struct Dft {
 #pragma unroll
         for (int k = 0; k < R / 2; k++) {
             const int j = k * (16 / R);  // W_R^k = W_16^j
-            float2 t;
-            if (j == 0) {
-                t = o[k];
-            } else if (j == 4) {
-                t = (DIR > 0) ? cmuli(o[k]) : make_float2(o[k].y, -o[k].x);
+            if (j == 4) {
+                // t = DIR i o: lanes cross, so scalar adds
+                const float tx = (DIR > 0) ? -o[k].y : o[k].y, ty = (DIR > 0) ? o[k].x : -o[k].x;
+                v[k] = make_float2(e[k].x + tx, e[k].y + ty);
+                v[k + R / 2] = make_float2(e[k].x - tx, e[k].y - ty);
             } else {
-                t = cmul(o[k], make_float2(w16c(j), DIR * w16s(j)));
+                const float2 t = (j == 0) ? o[k] : cmul(o[k], make_float2(w16c(j), DIR * w16s(j)));
+                v[k] = cadd(e[k], t);
+                v[k + R / 2] = csub(e[k], t);
             }
-            v[k] = cadd(e[k], t);
-            v[k + R / 2] = csub(e[k], t);
         }
     }
 };

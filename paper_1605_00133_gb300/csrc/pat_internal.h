@@ -38,6 +38,8 @@ struct Geom {
     int cs;                     // plane-kernel cluster size
     int len[3];                 // line length per axis (z, y, x)
     int ncols[3];               // lines per batch entry per axis, see Workspace::ms
+    int tc[3];                  // lines per tile of the state layout per axis (the line kernel's CTA)
+    int ntile[3];               // tiles per batch entry: ceil(ncols / tc)
     long long nreal, nspec;     // per batch entry: nz*ny*nx reals, nz*nxh*ny half-spectrum values
     long long nplane;           // nxh*ny: one plane's half spectrum
     int sensor_z;
@@ -47,7 +49,9 @@ struct Geom {
 
 struct DeviceTables {
     float2* tw[3];              // FFT twiddles exp(-2 pi i m / L) per axis length
-    float* kappa[3];            // kappa(|k|) at every point of every line of axis a: [len][ncols]
+    float2* twi[3];             // the same, per thread of a line pass (LineKernels in pat_kargs.h)
+    float2* twf[3];
+    float* kappa[3];            // kappa(|k|) at every point of every line of axis a: [ntile][len][tc]
     float2* dplus[3];           // i k exp(+i k dx/2) per axis, every bin of the axis
     float2* dminus[3];          // i k exp(-i k dx/2)
     float* coef[CT_COUNT][3];   // per-axis coefficient tables
@@ -55,7 +59,9 @@ struct DeviceTables {
 
 // Mixed representation: the split fields u_i, rho_i of axis i are kept with axis i in real space
 // and the other two axes Fourier transformed (the PML factor of axis i depends on x_i alone, so the
-// update is pointwise there).  Line c of axis i at position j sits at ms[i][s][(b*len + j)*ncols + c]:
+// update is pointwise there).  Lines are grouped in tiles of tc lines (the lines of one line-pass
+// CTA); line c of axis i at position j sits at
+// ms[i][s][((b*ntile + c/tc)*len + j)*tc + c%tc], the last tile padded with unused lines:
 //   z: c = kx*ny + ky              (kx <= nx/2)        ncols = nxh*ny
 //   y: c = kz*nxh + kx             (kx <= nx/2)        ncols = nz*nxh
 //   x: c = kz*ny + ky              (kz <= nz/2)        ncols = nzh*ny

@@ -72,11 +72,13 @@ struct LineArgs {
     int ncols;                  // lines per batch entry
     int mode, flags;
     const float2* tw;           // exp(-2 pi i m / L), m < L
+    const float2* twi;          // per-thread twiddles of the inverse transform's first half, [k][r]
+    const float2* twf;          // ... and of the forward transform's first half (LineKernels docs)
     const float2* in;           // 3D half spectrum read (LM_STEP, LM_INIT)
     float2* out;                // 3D half spectrum written or accumulated (LM_STEP, LM_FIN)
-    float2* st1;                // mixed-representation states [B][L][ncols]
+    float2* st1;                // mixed-representation states, tile-major [B][tile][L][TC]
     float2* st2;
-    const float* kap;           // kappa(|k|) at every line point [L][ncols]
+    const float* kap;           // kappa(|k|) at every line point, tile-major [tile][L][TC]
     const float2* dpre;         // k-space factor before the first inverse transform (NULL: none)
     const float2* dmid;         // between the two state updates
     const float2* dpost;        // after the last forward transform (NULL: none)
@@ -92,12 +94,21 @@ struct LineArgs {
 
 typedef void (*LineKernel)(LineArgs);
 
+// A length-L line transform is split L = ra * rb (pat_fft.cuh).  Thread r of a line (r < ra) uses
+// the twiddle tables
+//   twi[k * ra + r] = exp(+2 pi i r k / L), k < rb                 (inverse, k-space side first)
+//   twf[k * rb + r] = exp(-2 pi i r k / L), k < ra, r < rb         (forward, spatial side first)
+//   twf[k * ra + r] = exp(-2 pi i (r/2)(2k + r%2) / L), k < rb     (forward, when pair: ra = 2 rb)
 struct LineKernels {
     LineKernel pass[3] = {nullptr, nullptr, nullptr};  // by axis (z, y, x) for this line length
     size_t smem = 0;
-    int tc = 0;  // lines per CTA
+    int tc = 0;  // lines per CTA (one tile of the state layout)
     int nt = 0;  // threads per CTA
+    int ra = 0, rb = 0;
+    bool pair = false;
 };
+
+LineKernels line_kernels_for(int len);  // pass[] all NULL for a length without kernels
 
 LineKernels line_kernels_l8();
 LineKernels line_kernels_l16();

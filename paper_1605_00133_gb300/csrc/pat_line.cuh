@@ -38,6 +38,11 @@
 // before the x pass of the step passed its own wait, and is read through L2 (ld.cg, cp.async.cg).
 // No kernel waits on a grid whose CTAs have not all started, so the overlap cannot deadlock.
 //
+// States and kappa are stored tile-major, [B][tile][L][TC] (tile = line / TC, lines padded to a
+// whole tile), so a CTA's tile is one contiguous block and every access of a thread is its own base
+// plus a compile-time offset.  The twiddles of the two transform halves come from per-thread tables
+// (twi, twf: entry k of thread r at k * (row stride) + r) for the same reason.
+//
 // Spectrum access per axis (3D half spectrum [kz][kx][ky], kx <= nx/2):
 //   z lines (kx, ky): column access, stride nxh*ny
 //   y lines (kz, kx): each line is a contiguous row; the CTA's TC rows are one contiguous block,
@@ -70,6 +75,10 @@ struct LS {
     static constexpr int TILE = L * TC;          // one prefetched tile (float2)
     static constexpr size_t smem = (2 * (size_t)BUF + 3 * (size_t)TILE) * sizeof(float2);
     static constexpr int MINB = (NT >= 256) ? 2 : 4;
+    // exchange rows are swizzled (bit 0 of the row flipped by bit 0 of row / B) when a row is only
+    // half the banks
+    static constexpr bool SWZ = TC < 16;
+    static constexpr int TWF_STRIDE = PAIR ? A : B;  // row stride of the forward twiddle table
 };
 
 // W_R^(DIR k) = exp(DIR 2 pi i k / R), R in {2, 4, 8, 16}, k < R/2
@@ -92,8 +101,9 @@ struct LineCtx {
     int cl, r, col, col0, b;
     int xr, xh;     // spatial layout: row group and half (PAIR), else xr = r, xh = 0
     bool vcol, xact;
-    size_t sbase;   // state element of this line at position 0
+    size_t tbase;   // this CTA's tile of the states, element (j = 0, line 0)
     size_t pbase;   // this batch entry's 3D spectrum
+    float2 sgn;     // PAIR butterflies: (+1, +1) for the even half, (-1, -1) for the odd one
     int ka, kb;     // x lines: kz, ky
     int ma, mb;     // x lines: the mirror line's kz, ky
 
@@ -113,8 +123,9 @@ struct LineCtx {
         vcol = col < a.ncols;
         xact = vcol && (PAIR || r < B);
         b = blockIdx.y;
-        sbase = (size_t)b * L * a.ncols + col;
+        tbase = ((size_t)b * gridDim.x + blockIdx.x) * (size_t)(L * TC);
         pbase = (size_t)b * a.g.nspec;
+        sgn = xh ? make_float2(-1.f, -1.f) : make_float2(1.f, 1.f);
         ka = kb = ma = mb = 0;
         if (AX == 2) {
             const int ny = a.g.ny, nz = a.g.nz;
@@ -126,11 +137,39 @@ struct LineCtx {
     }
     // position along the line of spatial-layout value q
     __device__ __forceinline__ int xpos(int q) const { return PAIR ? xr + B * (XN * xh + q) : r + B * q; }
-    // exchange-buffer element of (row, this line).  With 8 lines a row is half the banks; rows that a
-    // half-warp touches together differ by 1, A or B, so bit 0 of the row is flipped by bit 0 of
-    // row / B to put them in different halves.
-    __device__ __forceinline__ int xo(int row) const {
-        return ((TC < 16) ? (row ^ ((row / B) & 1)) : row) * TC + cl;
+    // state element of this line at spatial-layout value q (tile-major layout)
+    __device__ __forceinline__ size_t sidx(int q) const { return tbase + (size_t)xpos(q) * TC + cl; }
+
+    // Exchange-buffer elements, layout [row][line].  With 8 lines a row is half the banks; rows that
+    // a half-warp touches together differ by 1, A or B, so bit 0 of the row is flipped by bit 0 of
+    // row / B to put them in different halves (S::SWZ).  Each access below writes row = (this
+    // thread's part) + (a compile-time part) and resolves the flip per thread, so the address is a
+    // per-thread base plus a constant:
+    //   inv, k-space side writes  row = k A + r        flip = (k A/B + r/B) & 1
+    //   inv, spatial side reads   row = r A + t        flip = (r A/B + t/B) & 1       (r < B)
+    //                   PAIR      row = xr A + 2q + xh flip = [q >= B/2]
+    //   fwd, spatial side writes  row = k B + r        flip = k & 1                   (r < B)
+    //                   PAIR      row = (2k + xh) B + xr  flip = xh
+    //   fwd, k-space side reads   row = r B + t        flip = r & 1
+    // (a flip changes bit 0 of the row, which is bit 0 of the thread's part in every case).
+    __device__ __forceinline__ int xo_inv_st(int k) const {
+        const int f = S::SWZ ? ((((A / B) % 2) ? k : 0) + r / B) & 1 : 0;
+        return (k * A + (r ^ f)) * TC + cl;
+    }
+    __device__ __forceinline__ int xo_inv_ld(int t) const {
+        if (PAIR) {
+            const int f = S::SWZ ? (t / 2 >= B / 2) : 0;  // t = 2q + xh is passed as 2q
+            return (xr * A + t + (xh ^ f)) * TC + cl;
+        }
+        const int f = S::SWZ ? (((A / B) % 2 ? r : 0) + t / B) & 1 : 0;
+        return (r * A + (t ^ f)) * TC + cl;
+    }
+    __device__ __forceinline__ int xo_fwd_st(int k) const {
+        if (PAIR) return (2 * k * B + xh * B + (xr ^ (S::SWZ ? xh : 0))) * TC + cl;
+        return (k * B + (r ^ (S::SWZ ? (k & 1) : 0))) * TC + cl;
+    }
+    __device__ __forceinline__ int xo_fwd_ld(int t) const {
+        return (r * B + (t ^ (S::SWZ ? (r & 1) : 0))) * TC + cl;
     }
 
     // ---- transforms between the layouts (every thread of the CTA must call these)
@@ -138,16 +177,17 @@ struct LineCtx {
     __device__ __forceinline__ void inv(float2* v, float2* x, float2* xb) const {
         if (vcol) {
             Dft<B, +1>::run(v);
+            const float2* tw = a.twi + r;  // W_L^{+r k}, k < B, row stride A
 #pragma unroll
             for (int k1p = 0; k1p < B; k1p++)
-                xb[xo(k1p * A + r)] = (k1p == 0) ? v[0] : cmul(v[k1p], twiddle<L, +1>(a.tw, r * k1p));
+                xb[xo_inv_st(k1p)] = (k1p == 0) ? v[0] : cmul(v[k1p], __ldg(tw + k1p * A));
         }
         __syncthreads();
         if (PAIR) {
             // A-point DFT of row group xr by decimation in time: this thread the even (xh = 0) or odd
             // inputs, then X[k] = E[k] + W_A^k O[k], X[k + A/2] = E[k] - W_A^k O[k]
 #pragma unroll
-            for (int q = 0; q < XN; q++) x[q] = vcol ? xb[xo(xr * A + 2 * q + xh)] : make_float2(0.f, 0.f);
+            for (int q = 0; q < XN; q++) x[q] = vcol ? xb[xo_inv_ld(2 * q)] : make_float2(0.f, 0.f);
             Dft<XN, +1>::run(x);
 #pragma unroll
             for (int k = 1; k < XN; k++)
@@ -156,11 +196,11 @@ struct LineCtx {
             for (int k = 0; k < XN; k++) {
                 const float2 t = make_float2(__shfl_xor_sync(0xffffffffu, x[k].x, TC),
                                              __shfl_xor_sync(0xffffffffu, x[k].y, TC));
-                x[k] = xh ? csub(t, x[k]) : cadd(x[k], t);
+                x[k] = csgn_add(sgn, x[k], t);  // E + W O (even half) or E - W O (odd half)
             }
         } else if (vcol && r < B) {
 #pragma unroll
-            for (int t = 0; t < A; t++) x[t] = xb[xo(r * A + t)];
+            for (int t = 0; t < A; t++) x[t] = xb[xo_inv_ld(t)];
             Dft<A, +1>::run(x);
         }
     }
@@ -173,29 +213,28 @@ struct LineCtx {
             for (int q = 0; q < XN; q++) {
                 const float2 t = make_float2(__shfl_xor_sync(0xffffffffu, x[q].x, TC),
                                              __shfl_xor_sync(0xffffffffu, x[q].y, TC));
-                x[q] = xh ? csub(t, x[q]) : cadd(x[q], t);
+                x[q] = csgn_add(sgn, x[q], t);  // x[q] + x[q + A/2] (even half) or their difference
             }
 #pragma unroll
             for (int q = 1; q < XN; q++)
                 if (xh) x[q] = cmul(x[q], wr<A, -1>(q));
             Dft<XN, -1>::run(x);
             if (vcol) {
+                const float2* tw = a.twf + r;  // W_L^{-xr (2k + xh)}, k < XN, row stride A
 #pragma unroll
-                for (int k = 0; k < XN; k++) {
-                    const int k1 = 2 * k + xh;
-                    xb[xo(k1 * B + xr)] = cmul(x[k], twiddle<L, -1>(a.tw, xr * k1));
-                }
+                for (int k = 0; k < XN; k++) xb[xo_fwd_st(k)] = cmul(x[k], __ldg(tw + k * A));
             }
         } else if (vcol && r < B) {
             Dft<A, -1>::run(x);
+            const float2* tw = a.twf + r;  // W_L^{-r k}, k < A, row stride B
 #pragma unroll
             for (int k1 = 0; k1 < A; k1++)
-                xb[xo(k1 * B + r)] = (k1 == 0) ? x[0] : cmul(x[k1], twiddle<L, -1>(a.tw, r * k1));
+                xb[xo_fwd_st(k1)] = (k1 == 0) ? x[0] : cmul(x[k1], __ldg(tw + k1 * B));
         }
         __syncthreads();
         if (vcol) {
 #pragma unroll
-            for (int t = 0; t < B; t++) v[t] = xb[xo(r * B + t)];
+            for (int t = 0; t < B; t++) v[t] = xb[xo_fwd_ld(t)];
             Dft<B, -1>::run(v);
         }
     }
@@ -312,23 +351,24 @@ struct LineCtx {
                     nv.x = fmaf(d, o.x, nv.x);
                     nv.y = fmaf(d, o.y, nv.y);
                 }
-                st[sbase + (size_t)j * a.ncols] = nv;
+                st[sidx(q)] = nv;
                 x[q] = c[2] ? cscale(nv, __ldg(c[2] + j)) : nv;
             }
         }
     }
 
     // issue the cp.async copy of one old state tile (one commit group; every thread commits it).
-    // 16-byte copies of column pairs (ncols and the tile start are even), so a thread's copies are
-    // not the values it later reads: consumers wait, then pass a barrier.
+    // The tile is one contiguous block (padding lines included) copied in 16-byte chunks, so a
+    // thread's copies are not the values it later reads: consumers wait, then pass a barrier.
     __device__ __forceinline__ void prefetch(const float2* __restrict__ st, float2* pf, bool on) const {
         constexpr int NCH = L * (TC / 2);  // 16-byte chunks per tile
+        static_assert(NCH % S::NT == 0, "tile chunks per thread");
         if (on) {
-            const int ncol2 = min(TC, a.ncols - col0) / 2;
-            const size_t base = (size_t)b * L * a.ncols + col0;
-            for (int q = threadIdx.x; q < NCH; q += S::NT) {
-                const int j = q / (TC / 2), cc = q % (TC / 2);
-                if (cc < ncol2) cp_async16(pf + j * TC + 2 * cc, st + base + (size_t)j * a.ncols + 2 * cc);
+            const float2* src = st + tbase;
+#pragma unroll
+            for (int q = 0; q < NCH / S::NT; q++) {
+                const int e = 2 * ((int)threadIdx.x + q * S::NT);
+                cp_async16(pf + e, src + e);
             }
         }
         cp_async_commit();
@@ -386,7 +426,7 @@ __global__ void __launch_bounds__(LS<L>::NT, LS<L>::MINB) line_pass_kernel(LineA
 #pragma unroll
         for (int q = 0; q < XN; q++) {
             const int j = c.xpos(q);
-            x[q] = c.xact ? cscale(a.st1[c.sbase + (size_t)j * a.ncols], __ldg(a.c1[0] + j)) : make_float2(0.f, 0.f);
+            x[q] = c.xact ? cscale(a.st1[c.sidx(q)], __ldg(a.c1[0] + j)) : make_float2(0.f, 0.f);
         }
         c.fwd(x, v, c.buf1);
         c.store_k(a.out, v, true, false);
@@ -404,15 +444,15 @@ __global__ void __launch_bounds__(LS<L>::NT, LS<L>::MINB) line_pass_kernel(LineA
         c.inv(v, x, c.buf0);
         if (c.xact) {
 #pragma unroll
-            for (int q = 0; q < XN; q++) a.st2[c.sbase + (size_t)c.xpos(q) * a.ncols] = x[q];
+            for (int q = 0; q < XN; q++) a.st2[c.sidx(q)] = x[q];
         }
         return;
     }
 
-    float kap[B];
+    float kap[B];  // tile-major like the states: this thread's points at r + A k2
+    const float* kp = a.kap + (size_t)blockIdx.x * (L * S::TC) + c.r * S::TC + c.cl;
 #pragma unroll
-    for (int k2 = 0; k2 < B; k2++)
-        kap[k2] = c.vcol ? __ldg(a.kap + (size_t)(c.r + A * k2) * a.ncols + c.col) : 0.f;
+    for (int k2 = 0; k2 < B; k2++) kap[k2] = c.vcol ? __ldg(kp + k2 * A * S::TC) : 0.f;
 
     c.factor(v, a.dpre, kap, a.s_pre);
     cp_async_wait<1>();  // state 1 has landed; the barrier inside inv() publishes it to every thread
@@ -473,6 +513,9 @@ LineKernels make_line_kernels() {
     k.smem = S::smem;
     k.tc = S::TC;
     k.nt = S::NT;
+    k.ra = S::A;
+    k.rb = S::B;
+    k.pair = S::PAIR;
     return k;
 }
 

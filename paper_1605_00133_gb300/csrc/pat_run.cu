@@ -40,7 +40,7 @@ static PlaneKernels plane_kernels_for(int nx, int ny) {
     }
 }
 
-static LineKernels line_kernels_for(int len) {
+LineKernels line_kernels_for(int len) {
     switch (len) {
         case 8: return line_kernels_l8();
         case 16: return line_kernels_l16();
@@ -199,6 +199,8 @@ static LineArgs line_base(const Geom& g, const DeviceTables& t, const Workspace&
     a.g = g;
     a.ncols = g.ncols[ax];
     a.tw = t.tw[ax];
+    a.twi = t.twi[ax];
+    a.twf = t.twf[ax];
     a.st1 = w.ms[ax][0];
     a.st2 = w.ms[ax][1];
     a.kap = t.kappa[ax];

@@ -73,8 +73,17 @@ struct LS {
     static constexpr int PITCH = (TC >= 16) ? L + 1 : L + 2;
     static constexpr int BUF = L * TC + 2 * TC;  // one exchange buffer (float2), also holds TC staged rows
     static constexpr int TILE = L * TC;          // one prefetched tile (float2)
-    static constexpr size_t smem = (2 * (size_t)BUF + 3 * (size_t)TILE) * sizeof(float2);
-    static constexpr int MINB = (NT >= 256) ? 2 : 4;
+    // Resident CTAs per SM the register budget is sized for: the target, or fewer where shared
+    // memory (228 KB per SM, 1 KB reserved per CTA) allows fewer.  Where three tiles would cut the
+    // CTAs below the target (long lines), the old output of y and z lines (pfo) reuses the state-1
+    // tile once every thread has read it.
+    static constexpr int MINB_T = (NT >= 256) ? 2 : 4;
+    static constexpr int SMEM_SM = 233472;
+    static constexpr bool PFO_ALIAS =
+        (int)(SMEM_SM / ((2 * (size_t)BUF + 3 * (size_t)TILE) * sizeof(float2) + 1024)) < MINB_T;
+    static constexpr size_t smem = (2 * (size_t)BUF + (PFO_ALIAS ? 2 : 3) * (size_t)TILE) * sizeof(float2);
+    static constexpr int MINB_S = (int)(SMEM_SM / (smem + 1024));
+    static constexpr int MINB = (MINB_T < MINB_S) ? MINB_T : (MINB_S > 0 ? MINB_S : 1);
     // exchange rows are swizzled (bit 0 of the row flipped by bit 0 of row / B) when a row is only
     // half the banks
     static constexpr bool SWZ = TC < 16;
@@ -112,7 +121,7 @@ struct LineCtx {
         buf1 = smem + S::BUF;
         pf1 = smem + 2 * S::BUF;
         pf2 = pf1 + S::TILE;
-        pfo = pf2 + S::TILE;
+        pfo = S::PFO_ALIAS ? pf1 : pf2 + S::TILE;
         const int tid = threadIdx.x;
         cl = tid % TC;
         r = tid / TC;
@@ -433,9 +442,13 @@ __global__ void __launch_bounds__(LS<L>::NT, LS<L>::MINB) line_pass_kernel(LineA
         return;
     }
 
+    float kap[B];  // tile-major like the states: this thread's points at r + A k2
     if (a.mode == LM_STEP) {
         c.prefetch(a.st1, c.pf1, (a.flags & LF_NO_OLD1) == 0);
         c.prefetch(a.st2, c.pf2, (a.flags & LF_NO_OLD2) == 0);
+        const float* kp = a.kap + (size_t)blockIdx.x * (L * S::TC) + c.r * S::TC + c.cl;
+#pragma unroll
+        for (int k2 = 0; k2 < B; k2++) kap[k2] = c.vcol ? __ldg(kp + k2 * A * S::TC) : 0.f;
     }
     c.load_k(a.in, v);
     if (a.mode == LM_INIT) {
@@ -449,11 +462,6 @@ __global__ void __launch_bounds__(LS<L>::NT, LS<L>::MINB) line_pass_kernel(LineA
         return;
     }
 
-    float kap[B];  // tile-major like the states: this thread's points at r + A k2
-    const float* kp = a.kap + (size_t)blockIdx.x * (L * S::TC) + c.r * S::TC + c.cl;
-#pragma unroll
-    for (int k2 = 0; k2 < B; k2++) kap[k2] = c.vcol ? __ldg(kp + k2 * A * S::TC) : 0.f;
-
     c.factor(v, a.dpre, kap, a.s_pre);
     cp_async_wait<1>();  // state 1 has landed; the barrier inside inv() publishes it to every thread
     c.inv(v, x, c.buf0);
@@ -461,6 +469,7 @@ __global__ void __launch_bounds__(LS<L>::NT, LS<L>::MINB) line_pass_kernel(LineA
     if (late) pdl_wait();  // the new spectrum is written by the preceding pass
     if (a.flags & LF_TRIGGER_MID) pdl_trigger();
     const bool pre = accum && AX != 2;
+    if (S::PFO_ALIAS && pre) __syncthreads();  // every thread's state-1 update has read pf1
     c.prefetch_out(pre);
     c.fwd(x, v, c.buf1);
     c.factor(v, a.dmid, kap, a.s_mid);

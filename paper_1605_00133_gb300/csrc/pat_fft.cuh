@@ -221,6 +221,14 @@ __device__ __forceinline__ void cluster_sync_relaxed() {
     asm volatile("barrier.cluster.arrive.relaxed.aligned;\n\tbarrier.cluster.wait.aligned;" ::: "memory");
 }
 
+// Read-only load that does not allocate in L1: for data read once per pass (kappa), so that it does
+// not evict the small per-axis tables that every phase of a line pass reads again.
+__device__ __forceinline__ float ldg_stream(const float* p) {
+    float v;
+    asm("ld.global.nc.L1::no_allocate.f32 %0, [%1];" : "=f"(v) : "l"(p));
+    return v;
+}
+
 // Asynchronous global -> shared copies (cp.async): the data land in shared memory without passing
 // through registers; a thread may read what it copied itself after cp_async_wait<N>() (at most N of
 // its committed groups still pending), other threads only after a barrier on top of that.

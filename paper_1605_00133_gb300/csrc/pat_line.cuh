@@ -79,9 +79,14 @@ struct LS {
     // tile once every thread has read it.
     static constexpr int MINB_T = (NT >= 256) ? 2 : 4;
     static constexpr int SMEM_SM = 233472;
-    static constexpr bool PFO_ALIAS =
-        (int)(SMEM_SM / ((2 * (size_t)BUF + 3 * (size_t)TILE) * sizeof(float2) + 1024)) < MINB_T;
-    static constexpr size_t smem = (2 * (size_t)BUF + (PFO_ALIAS ? 2 : 3) * (size_t)TILE) * sizeof(float2);
+    // the per-axis tables a time step reads in every phase (twiddles, k-space factors, state
+    // coefficients) are copied to shared memory at the start of a pass, up to L = 128
+    static constexpr bool STAGE = (L <= 128);
+    static constexpr int TAB2 = STAGE ? 5 * L : 0;  // float2: twi, twf, k-space factors pre/mid/post
+    static constexpr int TAB1 = STAGE ? 6 * L : 0;  // float: coefficients of state 1 and state 2
+    static constexpr size_t SBASE = (2 * (size_t)BUF + TAB2) * sizeof(float2) + TAB1 * sizeof(float);
+    static constexpr bool PFO_ALIAS = (int)(SMEM_SM / (SBASE + 3 * (size_t)TILE * sizeof(float2) + 1024)) < MINB_T;
+    static constexpr size_t smem = SBASE + (PFO_ALIAS ? 2 : 3) * (size_t)TILE * sizeof(float2);
     static constexpr int MINB_S = (int)(SMEM_SM / (smem + 1024));
     static constexpr int MINB = (MINB_T < MINB_S) ? MINB_T : (MINB_S > 0 ? MINB_S : 1);
     // exchange rows are swizzled (bit 0 of the row flipped by bit 0 of row / B) when a row is only
@@ -113,6 +118,10 @@ struct LineCtx {
     size_t tbase;   // this CTA's tile of the states, element (j = 0, line 0)
     size_t pbase;   // this batch entry's 3D spectrum
     float2 sgn;     // PAIR butterflies: (+1, +1) for the even half, (-1, -1) for the odd one
+    const float2* ti;  // this thread's twiddles (global tables, or their shared copies after stage())
+    const float2* tf;
+    float2* tab2;      // shared copies (S::STAGE): twi, twf, k-space factors [3]
+    float* tab1;       // ... state coefficients [2][3]
     int ka, kb;     // x lines: kz, ky
     int ma, mb;     // x lines: the mirror line's kz, ky
 
@@ -122,6 +131,8 @@ struct LineCtx {
         pf1 = smem + 2 * S::BUF;
         pf2 = pf1 + S::TILE;
         pfo = S::PFO_ALIAS ? pf1 : pf2 + S::TILE;
+        tab2 = pf2 + (S::PFO_ALIAS ? 1 : 2) * S::TILE;
+        tab1 = reinterpret_cast<float*>(tab2 + S::TAB2);
         const int tid = threadIdx.x;
         cl = tid % TC;
         r = tid / TC;
@@ -135,6 +146,8 @@ struct LineCtx {
         tbase = ((size_t)b * gridDim.x + blockIdx.x) * (size_t)(L * TC);
         pbase = (size_t)b * a.g.nspec;
         sgn = xh ? make_float2(-1.f, -1.f) : make_float2(1.f, 1.f);
+        ti = a.twi + r;
+        tf = a.twf + r;
         ka = kb = ma = mb = 0;
         if (AX == 2) {
             const int ny = a.g.ny, nz = a.g.nz;
@@ -143,6 +156,13 @@ struct LineCtx {
             ma = (nz - ka) & (nz - 1);
             mb = (ny - kb) & (ny - 1);
         }
+    }
+    // read a table entry: shared copies (S::STAGE) by plain loads, global tables through the
+    // read-only path
+    template <class T>
+    __device__ __forceinline__ static T rd(const T* p) {
+        if constexpr (S::STAGE) return *p;
+        else return __ldg(p);
     }
     // position along the line of spatial-layout value q
     __device__ __forceinline__ int xpos(int q) const { return PAIR ? xr + B * (XN * xh + q) : r + B * q; }
@@ -186,10 +206,10 @@ struct LineCtx {
     __device__ __forceinline__ void inv(float2* v, float2* x, float2* xb) const {
         if (vcol) {
             Dft<B, +1>::run(v);
-            const float2* tw = a.twi + r;  // W_L^{+r k}, k < B, row stride A
+            // W_L^{+r k}, k < B, row stride A
 #pragma unroll
             for (int k1p = 0; k1p < B; k1p++)
-                xb[xo_inv_st(k1p)] = (k1p == 0) ? v[0] : cmul(v[k1p], __ldg(tw + k1p * A));
+                xb[xo_inv_st(k1p)] = (k1p == 0) ? v[0] : cmul(v[k1p], rd(ti + k1p * A));
         }
         __syncthreads();
         if (PAIR) {
@@ -229,16 +249,16 @@ struct LineCtx {
                 if (xh) x[q] = cmul(x[q], wr<A, -1>(q));
             Dft<XN, -1>::run(x);
             if (vcol) {
-                const float2* tw = a.twf + r;  // W_L^{-xr (2k + xh)}, k < XN, row stride A
+                // W_L^{-xr (2k + xh)}, k < XN, row stride A
 #pragma unroll
-                for (int k = 0; k < XN; k++) xb[xo_fwd_st(k)] = cmul(x[k], __ldg(tw + k * A));
+                for (int k = 0; k < XN; k++) xb[xo_fwd_st(k)] = cmul(x[k], rd(tf + k * A));
             }
         } else if (vcol && r < B) {
             Dft<A, -1>::run(x);
-            const float2* tw = a.twf + r;  // W_L^{-r k}, k < A, row stride B
+            // W_L^{-r k}, k < A, row stride B
 #pragma unroll
             for (int k1 = 0; k1 < A; k1++)
-                xb[xo_fwd_st(k1)] = (k1 == 0) ? x[0] : cmul(x[k1], __ldg(tw + k1 * B));
+                xb[xo_fwd_st(k1)] = (k1 == 0) ? x[0] : cmul(x[k1], rd(tf + k1 * B));
         }
         __syncthreads();
         if (vcol) {
@@ -279,8 +299,8 @@ struct LineCtx {
 #pragma unroll
                 for (int k2 = 0; k2 < B; k2++) {
                     const int j = r + A * k2;
-                    if (k2 < B / 2 || (k2 == B / 2 && r == 0)) v[k2] = own[(size_t)j * ny];
-                    else v[k2] = cconj(mir[(size_t)(L - j) * ny]);
+                    if (k2 < B / 2 || (k2 == B / 2 && r == 0)) v[k2] = __ldcg(own + (size_t)j * ny);
+                    else v[k2] = cconj(__ldcg(mir + (size_t)(L - j) * ny));
                 }
             }
         }
@@ -353,15 +373,15 @@ struct LineCtx {
 #pragma unroll
             for (int q = 0; q < XN; q++) {
                 const int j = xpos(q);
-                float2 nv = cscale(x[q], __ldg(c[1] + j));
+                float2 nv = cscale(x[q], rd(c[1] + j));
                 if (!no_old) {
-                    const float d = __ldg(c[0] + j);
+                    const float d = rd(c[0] + j);
                     const float2 o = pf[j * TC + cl];
                     nv.x = fmaf(d, o.x, nv.x);
                     nv.y = fmaf(d, o.y, nv.y);
                 }
                 st[sidx(q)] = nv;
-                x[q] = c[2] ? cscale(nv, __ldg(c[2] + j)) : nv;
+                x[q] = c[2] ? cscale(nv, rd(c[2] + j)) : nv;
             }
         }
     }
@@ -403,13 +423,44 @@ struct LineCtx {
         cp_async_commit();
     }
 
+    // Copy the pass's tables to shared memory (one cp.async group, committed by every thread) and
+    // point ti/tf at the copies; d and c1, c2 receive the shared copies of a's factor and coefficient
+    // tables (NULL stays NULL).  The copies are read after a wait and a barrier.
+    __device__ __forceinline__ void stage(const float2** d, const float** c1, const float** c2) {
+        const int tid = threadIdx.x;
+        auto copy2 = [&](float2* dst, const float2* src) {
+            for (int q = tid; q < L / 2; q += S::NT) cp_async16(dst + 2 * q, src + 2 * q);
+        };
+        auto copy1 = [&](float* dst, const float* src) {
+            for (int q = tid; q < L / 4; q += S::NT) cp_async16(dst + 4 * q, src + 4 * q);
+        };
+        copy2(tab2, a.twi);
+        copy2(tab2 + L, a.twf);
+        const float2* dsrc[3] = {a.dpre, a.dmid, a.dpost};
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            d[i] = dsrc[i] ? tab2 + (2 + i) * L : nullptr;
+            if (dsrc[i]) copy2(tab2 + (2 + i) * L, dsrc[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < 3; i++) {
+            c1[i] = a.c1[i] ? tab1 + i * L : nullptr;
+            if (a.c1[i]) copy1(tab1 + i * L, a.c1[i]);
+            c2[i] = a.c2[i] ? tab1 + (3 + i) * L : nullptr;
+            if (a.c2[i]) copy1(tab1 + (3 + i) * L, a.c2[i]);
+        }
+        cp_async_commit();
+        ti = tab2 + r;
+        tf = tab2 + L + r;
+    }
+
     // k-space factor D[j] kappa s (D == NULL: s)
     __device__ __forceinline__ void factor(float2* v, const float2* __restrict__ D, const float* kap,
                                            float s) const {
         if (vcol) {
 #pragma unroll
             for (int k2 = 0; k2 < B; k2++) {
-                if (D) v[k2] = cmul(v[k2], cscale(__ldg(D + r + A * k2), kap[k2] * s));
+                if (D) v[k2] = cmul(v[k2], cscale(rd(D + r + A * k2), kap[k2] * s));
                 else v[k2] = cscale(v[k2], s);
             }
         }
@@ -443,12 +494,16 @@ __global__ void __launch_bounds__(LS<L>::NT, LS<L>::MINB) line_pass_kernel(LineA
     }
 
     float kap[B];  // tile-major like the states: this thread's points at r + A k2
+    const float2* dk[3] = {a.dpre, a.dmid, a.dpost};
+    const float* c1[3] = {a.c1[0], a.c1[1], a.c1[2]};
+    const float* c2[3] = {a.c2[0], a.c2[1], a.c2[2]};
     if (a.mode == LM_STEP) {
+        if (S::STAGE) c.stage(dk, c1, c2);
         c.prefetch(a.st1, c.pf1, (a.flags & LF_NO_OLD1) == 0);
         c.prefetch(a.st2, c.pf2, (a.flags & LF_NO_OLD2) == 0);
         const float* kp = a.kap + (size_t)blockIdx.x * (L * S::TC) + c.r * S::TC + c.cl;
 #pragma unroll
-        for (int k2 = 0; k2 < B; k2++) kap[k2] = c.vcol ? __ldg(kp + k2 * A * S::TC) : 0.f;
+        for (int k2 = 0; k2 < B; k2++) kap[k2] = c.vcol ? ldg_stream(kp + k2 * A * S::TC) : 0.f;
     }
     c.load_k(a.in, v);
     if (a.mode == LM_INIT) {
@@ -462,23 +517,27 @@ __global__ void __launch_bounds__(LS<L>::NT, LS<L>::MINB) line_pass_kernel(LineA
         return;
     }
 
-    c.factor(v, a.dpre, kap, a.s_pre);
+    if (S::STAGE) {
+        cp_async_wait<2>();  // the tables have landed (the states may still be in flight)
+        __syncthreads();
+    }
+    c.factor(v, dk[0], kap, a.s_pre);
     cp_async_wait<1>();  // state 1 has landed; the barrier inside inv() publishes it to every thread
     c.inv(v, x, c.buf0);
-    c.update(a.st1, a.c1, (a.flags & LF_NO_OLD1) != 0, c.pf1, x);
+    c.update(a.st1, c1, (a.flags & LF_NO_OLD1) != 0, c.pf1, x);
     if (late) pdl_wait();  // the new spectrum is written by the preceding pass
     if (a.flags & LF_TRIGGER_MID) pdl_trigger();
     const bool pre = accum && AX != 2;
     if (S::PFO_ALIAS && pre) __syncthreads();  // every thread's state-1 update has read pf1
     c.prefetch_out(pre);
     c.fwd(x, v, c.buf1);
-    c.factor(v, a.dmid, kap, a.s_mid);
+    c.factor(v, dk[1], kap, a.s_mid);
     cp_async_wait<1>();  // state 2 likewise (the old output may still be in flight)
     c.inv(v, x, c.buf0);
-    c.update(a.st2, a.c2, (a.flags & LF_NO_OLD2) != 0, c.pf2, x);
+    c.update(a.st2, c2, (a.flags & LF_NO_OLD2) != 0, c.pf2, x);
     cp_async_wait<0>();  // old output; published by the barrier inside fwd()
     c.fwd(x, v, c.buf1);
-    c.factor(v, a.dpost, kap, a.s_post);
+    c.factor(v, dk[2], kap, a.s_post);
 
     if (AX == 0 && (a.flags & LF_INJECT) && c.vcol) {
         const float2 sv = a.inj[(size_t)c.b * a.plane_bs + c.col];

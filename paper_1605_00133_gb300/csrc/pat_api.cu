@@ -154,6 +154,7 @@ pat_status build_tables(pat_grid* G) {
     const int n[3] = {d.nz, d.ny, d.nx};
     const double dt = G->s.dt;
     pat_status st;
+    std::vector<float2> h_twi[3], h_twf[3], h_dp[3], h_dm[3];  // host copies for the per-pass blocks
     // twiddles
     for (int a = 0; a < 3; a++) {
         std::vector<float2> tw(n[a]);
@@ -178,6 +179,8 @@ pat_status build_tables(pat_grid* G) {
         }
         if ((st = upload(G, &G->t.twi[a], twi, "twiddles")) != PAT_OK) return st;
         if ((st = upload(G, &G->t.twf[a], twf, "twiddles")) != PAT_OK) return st;
+        h_twi[a] = twi;
+        h_twf[a] = twf;
     }
     // derivative factors, every bin of each axis
     for (int a = 0; a < 3; a++) {
@@ -193,6 +196,8 @@ pat_status build_tables(pat_grid* G) {
         }
         if ((st = upload(G, &G->t.dplus[a], dp, "dplus")) != PAT_OK) return st;
         if ((st = upload(G, &G->t.dminus[a], dm, "dminus")) != PAT_OK) return st;
+        h_dp[a] = dp;
+        h_dm[a] = dm;
     }
     // kappa at every line point of each axis, tile-major [ntile][len][tc] like the states
     // (pat_internal.h); padding lines 0
@@ -217,7 +222,7 @@ pat_status build_tables(pat_grid* G) {
             if ((st = upload(G, &G->t.kappa[a], kap, "kappa")) != PAT_OK) return st;
         }
     }
-    // PML-derived coefficient tables
+    // PML-derived coefficient tables, and the per-pass table blocks
     for (int a = 0; a < 3; a++) {
         std::vector<std::vector<float>> ct(CT_COUNT, std::vector<float>(n[a]));
         for (int j = 0; j < n[a]; j++) {
@@ -238,6 +243,24 @@ pat_status build_tables(pat_grid* G) {
         }
         for (int c = 0; c < CT_COUNT; c++)
             if ((st = upload(G, &G->t.coef[c][a], ct[c], "coef")) != PAT_OK) return st;
+        const int L = n[a];
+        for (int ps = 0; ps < PS_COUNT; ps++) {
+            const PassTables& pt = kPassTables[ps];
+            std::vector<float2> blk(8 * (size_t)L, make_float2(0.f, 0.f));  // 5L float2 + 6L float
+            std::copy(h_twi[a].begin(), h_twi[a].end(), blk.begin());
+            std::copy(h_twf[a].begin(), h_twf[a].end(), blk.begin() + L);
+            for (int i = 0; i < 3; i++) {
+                if (pt.d[i] == DF_PLUS) std::copy(h_dp[a].begin(), h_dp[a].end(), blk.begin() + (2 + i) * L);
+                if (pt.d[i] == DF_MINUS) std::copy(h_dm[a].begin(), h_dm[a].end(), blk.begin() + (2 + i) * L);
+            }
+            float* c1 = reinterpret_cast<float*>(blk.data() + 5 * L);
+            for (int i = 0; i < 3; i++)
+                for (int j = 0; j < L; j++) {
+                    c1[i * L + j] = ct[pt.c1[i]][j];
+                    c1[(3 + i) * L + j] = ct[pt.c2[i]][j];
+                }
+            if ((st = upload(G, &G->t.pass[ps][a], blk, "pass tables")) != PAT_OK) return st;
+        }
     }
     return PAT_OK;
 }

@@ -31,6 +31,23 @@ enum CoefTable {
     CT_COUNT
 };
 
+// The tables one line pass of a time step reads, per kind of step: the k-space factor before,
+// between and after its transforms (none, i k e^{+ik dx/2}, i k e^{-ik dx/2}) and the coefficient
+// tables (decay, input gain, output gain) of its two states; an output gain CT_ONE means none.
+enum DFactor { DF_NONE = 0, DF_PLUS, DF_MINUS };
+enum PassSet { PS_FWD0 = 0, PS_FWD, PS_ADJ, PS_ADJ0, PS_COUNT };  // forward n = 0, n > 0; adjoint n > 0, n = 0
+struct PassTables {
+    int d[3];
+    int c1[3];
+    int c2[3];
+};
+static const PassTables kPassTables[PS_COUNT] = {
+    {{DF_PLUS, DF_MINUS, DF_NONE}, {CT_AS2, CT_VF0_G, CT_ONE}, {CT_A2, CT_DF_D, CT_ONE}},
+    {{DF_PLUS, DF_MINUS, DF_NONE}, {CT_AS2, CT_VF_G, CT_ONE}, {CT_A2, CT_DF_D, CT_ONE}},
+    {{DF_NONE, DF_PLUS, DF_MINUS}, {CT_A2, CT_C2, CT_A}, {CT_AS2, CT_VA_G, CT_AS}},
+    {{DF_NONE, DF_PLUS, DF_MINUS}, {CT_A2, CT_C2, CT_A}, {CT_AS2, CT_VA_G, CT_VA0_OUT}},
+};
+
 struct Geom {
     int nz, ny, nx, nxh;        // nxh = nx/2 + 1
     int nzh;                    // nz/2 + 1
@@ -55,6 +72,10 @@ struct DeviceTables {
     float2* dplus[3];           // i k exp(+i k dx/2) per axis, every bin of the axis
     float2* dminus[3];          // i k exp(-i k dx/2)
     float* coef[CT_COUNT][3];   // per-axis coefficient tables
+    // per pass set and axis, the tables of one line pass in one block, copied to shared memory at
+    // the start of the pass: twi, twf, the three k-space factors (len float2 each; zeros for none),
+    // then the coefficient tables of state 1 and state 2 (len floats each)
+    float2* pass[PS_COUNT][3];
 };
 
 // Mixed representation: the split fields u_i, rho_i of axis i are kept with axis i in real space

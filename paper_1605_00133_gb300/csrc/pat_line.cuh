@@ -423,33 +423,22 @@ struct LineCtx {
         cp_async_commit();
     }
 
-    // Copy the pass's tables to shared memory (one cp.async group, committed by every thread) and
-    // point ti/tf at the copies; d and c1, c2 receive the shared copies of a's factor and coefficient
-    // tables (NULL stays NULL).  The copies are read after a wait and a barrier.
+    // Copy the pass's table block (a.tabs: twi, twf, three k-space factors, six coefficient tables)
+    // to shared memory (one cp.async group, committed by every thread) and point ti/tf at the copies;
+    // d and c1, c2 receive the shared copies of a's factor and coefficient tables (NULL stays NULL).
+    // The copies are read after a wait and a barrier.
     __device__ __forceinline__ void stage(const float2** d, const float** c1, const float** c2) {
-        const int tid = threadIdx.x;
-        auto copy2 = [&](float2* dst, const float2* src) {
-            for (int q = tid; q < L / 2; q += S::NT) cp_async16(dst + 2 * q, src + 2 * q);
-        };
-        auto copy1 = [&](float* dst, const float* src) {
-            for (int q = tid; q < L / 4; q += S::NT) cp_async16(dst + 4 * q, src + 4 * q);
-        };
-        copy2(tab2, a.twi);
-        copy2(tab2 + L, a.twf);
+        constexpr int NCH = (S::TAB2 * (int)sizeof(float2) + S::TAB1 * (int)sizeof(float)) / 16;
+#pragma unroll
+        for (int q = threadIdx.x; q < NCH; q += S::NT) cp_async16(tab2 + 2 * q, a.tabs + 2 * q);
+        cp_async_commit();
         const float2* dsrc[3] = {a.dpre, a.dmid, a.dpost};
 #pragma unroll
         for (int i = 0; i < 3; i++) {
             d[i] = dsrc[i] ? tab2 + (2 + i) * L : nullptr;
-            if (dsrc[i]) copy2(tab2 + (2 + i) * L, dsrc[i]);
-        }
-#pragma unroll
-        for (int i = 0; i < 3; i++) {
             c1[i] = a.c1[i] ? tab1 + i * L : nullptr;
-            if (a.c1[i]) copy1(tab1 + i * L, a.c1[i]);
             c2[i] = a.c2[i] ? tab1 + (3 + i) * L : nullptr;
-            if (a.c2[i]) copy1(tab1 + (3 + i) * L, a.c2[i]);
         }
-        cp_async_commit();
         ti = tab2 + r;
         tf = tab2 + L + r;
     }

@@ -211,10 +211,24 @@ static LineArgs line_base(const Geom& g, const DeviceTables& t, const Workspace&
 }
 
 // state coefficient tables; an output gain of CT_ONE is passed as NULL (no multiply)
-static void set_coef(const float** dst, const DeviceTables& t, int ax, int c0, int c1, int c2) {
-    dst[0] = t.coef[c0][ax];
-    dst[1] = t.coef[c1][ax];
-    dst[2] = (c2 == CT_ONE) ? nullptr : t.coef[c2][ax];
+static void set_coef(const float** dst, const DeviceTables& t, int ax, const int* c) {
+    dst[0] = t.coef[c[0]][ax];
+    dst[1] = t.coef[c[1]][ax];
+    dst[2] = (c[2] == CT_ONE) ? nullptr : t.coef[c[2]][ax];
+}
+
+// the tables of one kind of time step (kPassTables) for a line pass of axis ax
+static void set_pass_tables(LineArgs& a, const DeviceTables& t, int ax, int ps) {
+    const PassTables& pt = kPassTables[ps];
+    const float2* d[3];
+    for (int i = 0; i < 3; i++)
+        d[i] = (pt.d[i] == DF_PLUS) ? t.dplus[ax] : (pt.d[i] == DF_MINUS) ? t.dminus[ax] : nullptr;
+    a.dpre = d[0];
+    a.dmid = d[1];
+    a.dpost = d[2];
+    set_coef(a.c1, t, ax, pt.c1);
+    set_coef(a.c2, t, ax, pt.c2);
+    a.tabs = t.pass[ps][ax];
 }
 
 cudaError_t run_forward(const Geom& g, const DeviceTables& t, const Workspace& w, const Scalars& s,
@@ -259,13 +273,9 @@ cudaError_t run_forward(const Geom& g, const DeviceTables& t, const Workspace& w
         for (int ax = 0; ax < 3; ax++) {
             la[ax] = line_base(g, t, w, ax);
             la[ax].mode = LM_STEP;
-            la[ax].dpre = t.dplus[ax];
-            la[ax].dmid = t.dminus[ax];
-            la[ax].dpost = nullptr;
             la[ax].s_pre = (float)(1.0 / g.len[ax]);
             la[ax].s_mid = (float)(1.0 / g.len[ax]);
             la[ax].s_post = (float)c2;
-            set_coef(la[ax].c2, t, ax, CT_A2, CT_DF_D, CT_ONE);
         }
         for (int n = 0; n + 1 < g.T; n++) {
             float2* cur = w.ph[n & 1];
@@ -274,7 +284,7 @@ cudaError_t run_forward(const Geom& g, const DeviceTables& t, const Workspace& w
                 LineArgs& a = la[ax];
                 a.in = cur;
                 a.out = nxt;
-                set_coef(a.c1, t, ax, CT_AS2, (n == 0) ? CT_VF0_G : CT_VF_G, CT_ONE);
+                set_pass_tables(a, t, ax, (n == 0) ? PS_FWD0 : PS_FWD);
                 a.flags = (n == 0 ? LF_NO_OLD1 : 0) | (ax == AX ? 0 : LF_ACCUM | LF_LATE_WAIT) |
                           (ax == AZ ? LF_RECORD : 0) | kTrigger[ax];
                 a.rec = w.rk + (size_t)(n + 1) * g.nplane;
@@ -328,13 +338,9 @@ cudaError_t run_adjoint(const Geom& g, const DeviceTables& t, const Workspace& w
     for (int ax = 0; ax < 3; ax++) {
         la[ax] = line_base(g, t, w, ax);
         la[ax].mode = LM_STEP;
-        la[ax].dpre = nullptr;
-        la[ax].dmid = t.dplus[ax];
-        la[ax].dpost = t.dminus[ax];
         la[ax].s_pre = (float)(1.0 / g.len[ax]);
         la[ax].s_mid = (float)(1.0 / g.len[ax]);
         la[ax].s_post = (float)(s.dt / s.rho0);
-        set_coef(la[ax].c1, t, ax, CT_A2, CT_C2, CT_A);
     }
     int cur = 0;
     for (int n = g.T - 2; n >= 0; n--) {
@@ -342,7 +348,7 @@ cudaError_t run_adjoint(const Geom& g, const DeviceTables& t, const Workspace& w
             LineArgs& a = la[ax];
             a.in = w.ph[cur];
             a.out = w.ph[cur ^ 1];
-            set_coef(a.c2, t, ax, CT_AS2, CT_VA_G, (n == 0) ? CT_VA0_OUT : CT_AS);
+            set_pass_tables(a, t, ax, (n == 0) ? PS_ADJ0 : PS_ADJ);
             a.flags = (n == g.T - 2 ? (LF_NO_OLD1 | LF_NO_OLD2) : 0) | (ax == AX ? 0 : LF_ACCUM | LF_LATE_WAIT) |
                       (ax == AZ ? LF_INJECT : 0) | kTrigger[ax];
             a.inj = w.rk + (size_t)n * g.nplane;

@@ -31,7 +31,7 @@ if ROOT not in sys.path:
 METRIC = "A+A^T pairs/s (64x128x128, 400 steps)"
 
 # (kernel source hash, workload, batch) -> DRAM bytes (read + write) of one time step, from ncu
-STEP_TRAFFIC = {("12046888789f", "c2", 1): 53.53e6}
+STEP_TRAFFIC = {("e5079acc7a28", "c2", 1): 53.50e6}
 UNIT = "pairs/s"
 
 
@@ -351,8 +351,8 @@ def main():
                  "fista_iterations": rep["inner_total"], "restarts": rep["restarts"],
                  "residuals": rep["residuals"], "rel_err_vs_phantom": float((prec - p0).norm() / p0.norm()),
                  "plain_seconds_to_2pct": t2, "trajectory": traj,
-                 "warm_seconds_to_2pct": None,
-                 "warm_start": "not built (learned U-Net warm start); the plain cold-start solve is timed"}
+                 "warm_start": "plain cold-start solve; --warm trains the learned U-Net warm start and "
+                               "times warm against plain (the line's warm_start object)"}
 
     warm = None
     if args.warm and B == 1:

@@ -172,7 +172,11 @@ pat_status build_tables(pat_grid* G) {
             for (int r = 0; r < ra; r++) twi[k * ra + r] = make_float2(tw[(r * k) % L].x, -tw[(r * k) % L].y);
         if (lk.pair) {
             for (int k = 0; k < rb; k++)
-                for (int r = 0; r < ra; r++) twf[k * ra + r] = tw[((r / 2) * (2 * k + r % 2)) % L];
+                for (int r = 0; r < ra; r++) {
+                    const int xr = lk.pnew ? ((r & 1) | ((r >> 2) << 1)) : r / 2;
+                    const int xh = lk.pnew ? ((r >> 1) & 1) : r % 2;
+                    twf[k * ra + r] = tw[(xr * (2 * k + xh)) % L];
+                }
         } else {
             for (int k = 0; k < ra; k++)
                 for (int r = 0; r < rb; r++) twf[k * rb + r] = tw[(r * k) % L];
@@ -246,7 +250,9 @@ pat_status build_tables(pat_grid* G) {
         const int L = n[a];
         for (int ps = 0; ps < PS_COUNT; ps++) {
             const PassTables& pt = kPassTables[ps];
-            std::vector<float2> blk(8 * (size_t)L, make_float2(0.f, 0.f));  // 5L float2 + 6L float
+            // 5 L float2, then 6 coefficient tables of L + 2 floats (entry j at j + 2 [j >= L/2])
+            const int cs = L + 2;
+            std::vector<float2> blk(5 * (size_t)L + 3 * (size_t)cs, make_float2(0.f, 0.f));
             std::copy(h_twi[a].begin(), h_twi[a].end(), blk.begin());
             std::copy(h_twf[a].begin(), h_twf[a].end(), blk.begin() + L);
             for (int i = 0; i < 3; i++) {
@@ -256,8 +262,9 @@ pat_status build_tables(pat_grid* G) {
             float* c1 = reinterpret_cast<float*>(blk.data() + 5 * L);
             for (int i = 0; i < 3; i++)
                 for (int j = 0; j < L; j++) {
-                    c1[i * L + j] = ct[pt.c1[i]][j];
-                    c1[(3 + i) * L + j] = ct[pt.c2[i]][j];
+                    const int jp = j + ((2 * j >= L) ? 2 : 0);
+                    c1[i * cs + jp] = ct[pt.c1[i]][j];
+                    c1[(3 + i) * cs + jp] = ct[pt.c2[i]][j];
                 }
             if ((st = upload(G, &G->t.pass[ps][a], blk, "pass tables")) != PAT_OK) return st;
         }

@@ -74,7 +74,8 @@ struct DeviceTables {
     float* coef[CT_COUNT][3];   // per-axis coefficient tables
     // per pass set and axis, the tables of one line pass in one block, copied to shared memory at
     // the start of the pass: twi, twf, the three k-space factors (len float2 each; zeros for none),
-    // then the coefficient tables of state 1 and state 2 (len floats each)
+    // then the coefficient tables of state 1 and state 2 (len + 2 floats each, entry j at
+    // j + 2 [j >= len/2])
     float2* pass[PS_COUNT][3];
 };
 

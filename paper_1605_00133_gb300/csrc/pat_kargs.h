@@ -99,7 +99,9 @@ typedef void (*LineKernel)(LineArgs);
 // the twiddle tables
 //   twi[k * ra + r] = exp(+2 pi i r k / L), k < rb                 (inverse, k-space side first)
 //   twf[k * rb + r] = exp(-2 pi i r k / L), k < ra, r < rb         (forward, spatial side first)
-//   twf[k * ra + r] = exp(-2 pi i (r/2)(2k + r%2) / L), k < rb     (forward, when pair: ra = 2 rb)
+//   twf[k * ra + r] = exp(-2 pi i xr (2k + xh) / L), k < rb        (forward, when pair: ra = 2 rb)
+// where a pair's row group and half are xr = r/2, xh = r%2, or with pnew xh = bit 1 of r and xr
+// the other bits of r
 struct LineKernels {
     LineKernel pass[3] = {nullptr, nullptr, nullptr};  // by axis (z, y, x) for this line length
     size_t smem = 0;
@@ -107,6 +109,7 @@ struct LineKernels {
     int nt = 0;  // threads per CTA
     int ra = 0, rb = 0;
     bool pair = false;
+    bool pnew = false;
 };
 
 LineKernels line_kernels_for(int len);  // pass[] all NULL for a length without kernels

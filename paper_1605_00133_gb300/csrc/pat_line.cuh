@@ -83,7 +83,10 @@ struct LS {
     // coefficients) are copied to shared memory at the start of a pass, up to L = 128
     static constexpr bool STAGE = (L <= 128);
     static constexpr int TAB2 = STAGE ? 5 * L : 0;  // float2: twi, twf, k-space factors pre/mid/post
-    static constexpr int TAB1 = STAGE ? 6 * L : 0;  // float: coefficients of state 1 and state 2
+    // float: coefficients of state 1 and state 2, L + 2 each: entry j at j + 2 [j >= L/2], so that
+    // the two halves of a thread pair (positions L/2 apart) read different banks
+    static constexpr int CSTR = L + 2;
+    static constexpr int TAB1 = STAGE ? 6 * CSTR : 0;
     static constexpr size_t SBASE = (2 * (size_t)BUF + TAB2) * sizeof(float2) + TAB1 * sizeof(float);
     static constexpr bool PFO_ALIAS = (int)(SMEM_SM / (SBASE + 3 * (size_t)TILE * sizeof(float2) + 1024)) < MINB_T;
     static constexpr size_t smem = SBASE + (PFO_ALIAS ? 2 : 3) * (size_t)TILE * sizeof(float2);
@@ -92,6 +95,12 @@ struct LS {
     // exchange rows are swizzled (bit 0 of the row flipped by bit 0 of row / B) when a row is only
     // half the banks
     static constexpr bool SWZ = TC < 16;
+    // Thread pairs.  With 8 lines per CTA a half-warp holds two rows r of the k-space layout.  If the
+    // two halves of a pair were rows r and r + 1, a half-warp would read its state tiles at positions
+    // L/2 apart (same banks); so then the pair is rows r and r + 2 (xh = bit 1 of r, xr = the other
+    // bits) and the exchange flip also takes bit 0 of row / A.
+    static constexpr bool PNEW = PAIR && TC <= 8;
+    static constexpr int PD = PNEW ? 2 : 1;  // pair partner: thread index ^ (PD * TC)
     static constexpr int TWF_STRIDE = PAIR ? A : B;  // row stride of the forward twiddle table
 };
 
@@ -136,8 +145,8 @@ struct LineCtx {
         const int tid = threadIdx.x;
         cl = tid % TC;
         r = tid / TC;
-        xr = PAIR ? (r >> 1) : r;
-        xh = PAIR ? (r & 1) : 0;
+        xr = PAIR ? (S::PNEW ? ((r & 1) | ((r >> 2) << 1)) : (r >> 1)) : r;
+        xh = PAIR ? (S::PNEW ? ((r >> 1) & 1) : (r & 1)) : 0;
         col0 = blockIdx.x * TC;
         col = col0 + cl;
         vcol = col < a.ncols;
@@ -166,39 +175,43 @@ struct LineCtx {
     }
     // position along the line of spatial-layout value q
     __device__ __forceinline__ int xpos(int q) const { return PAIR ? xr + B * (XN * xh + q) : r + B * q; }
+    // whether spatial-layout value q sits at a position >= L/2 (the odd half of a thread pair, or a
+    // thread's upper values)
+    __device__ __forceinline__ int upper(int q) const { return PAIR ? xh : (q >= XN / 2 ? 1 : 0); }
     // state element of this line at spatial-layout value q (tile-major layout)
     __device__ __forceinline__ size_t sidx(int q) const { return tbase + (size_t)xpos(q) * TC + cl; }
 
     // Exchange-buffer elements, layout [row][line].  With 8 lines a row is half the banks; rows that
     // a half-warp touches together differ by 1, A or B, so bit 0 of the row is flipped by bit 0 of
-    // row / B to put them in different halves (S::SWZ).  Each access below writes row = (this
-    // thread's part) + (a compile-time part) and resolves the flip per thread, so the address is a
-    // per-thread base plus a constant:
-    //   inv, k-space side writes  row = k A + r        flip = (k A/B + r/B) & 1
+    // row / B (and, with S::PNEW, also by bit 0 of row / A) to put them in different halves
+    // (S::SWZ).  Each access below writes row = (this thread's part) + (a compile-time part) and
+    // resolves the flip per thread, so the address is a per-thread base plus a constant:
+    //   inv, k-space side writes  row = k A + r        flip = (k A/B + r/B) & 1   (PNEW: ^ k & 1)
     //   inv, spatial side reads   row = r A + t        flip = (r A/B + t/B) & 1       (r < B)
-    //                   PAIR      row = xr A + 2q + xh flip = [q >= B/2]
+    //                   PAIR      row = xr A + 2q + xh flip = [q >= B/2]          (PNEW: ^ xr & 1)
     //   fwd, spatial side writes  row = k B + r        flip = k & 1                   (r < B)
-    //                   PAIR      row = (2k + xh) B + xr  flip = xh
-    //   fwd, k-space side reads   row = r B + t        flip = r & 1
+    //                   PAIR      row = (2k + xh) B + xr  flip = xh               (PNEW: ^ k & 1)
+    //   fwd, k-space side reads   row = r B + t        flip = r & 1               (PNEW: ^ r/2 & 1)
     // (a flip changes bit 0 of the row, which is bit 0 of the thread's part in every case).
     __device__ __forceinline__ int xo_inv_st(int k) const {
-        const int f = S::SWZ ? ((((A / B) % 2) ? k : 0) + r / B) & 1 : 0;
+        const int f = S::SWZ ? ((((A / B) % 2) ? k : 0) + r / B + (S::PNEW ? k : 0)) & 1 : 0;
         return (k * A + (r ^ f)) * TC + cl;
     }
     __device__ __forceinline__ int xo_inv_ld(int t) const {
         if (PAIR) {
-            const int f = S::SWZ ? (t / 2 >= B / 2) : 0;  // t = 2q + xh is passed as 2q
+            // t = 2q + xh is passed as 2q
+            const int f = S::SWZ ? ((t / 2 >= B / 2 ? 1 : 0) ^ (S::PNEW ? (xr & 1) : 0)) : 0;
             return (xr * A + t + (xh ^ f)) * TC + cl;
         }
         const int f = S::SWZ ? (((A / B) % 2 ? r : 0) + t / B) & 1 : 0;
         return (r * A + (t ^ f)) * TC + cl;
     }
     __device__ __forceinline__ int xo_fwd_st(int k) const {
-        if (PAIR) return (2 * k * B + xh * B + (xr ^ (S::SWZ ? xh : 0))) * TC + cl;
+        if (PAIR) return (2 * k * B + xh * B + (xr ^ (S::SWZ ? (xh ^ (S::PNEW ? (k & 1) : 0)) : 0))) * TC + cl;
         return (k * B + (r ^ (S::SWZ ? (k & 1) : 0))) * TC + cl;
     }
     __device__ __forceinline__ int xo_fwd_ld(int t) const {
-        return (r * B + (t ^ (S::SWZ ? (r & 1) : 0))) * TC + cl;
+        return (r * B + (t ^ (S::SWZ ? ((r ^ (S::PNEW ? (r >> 1) : 0)) & 1) : 0))) * TC + cl;
     }
 
     // ---- transforms between the layouts (every thread of the CTA must call these)
@@ -223,8 +236,8 @@ struct LineCtx {
                 if (xh) x[k] = cmul(x[k], wr<A, +1>(k));
 #pragma unroll
             for (int k = 0; k < XN; k++) {
-                const float2 t = make_float2(__shfl_xor_sync(0xffffffffu, x[k].x, TC),
-                                             __shfl_xor_sync(0xffffffffu, x[k].y, TC));
+                const float2 t = make_float2(__shfl_xor_sync(0xffffffffu, x[k].x, S::PD * TC),
+                                             __shfl_xor_sync(0xffffffffu, x[k].y, S::PD * TC));
                 x[k] = csgn_add(sgn, x[k], t);  // E + W O (even half) or E - W O (odd half)
             }
         } else if (vcol && r < B) {
@@ -240,8 +253,8 @@ struct LineCtx {
             // (x[q] - x[q + A/2]) W_A^-q (xh = 1); this thread holds x[q + xh A/2]
 #pragma unroll
             for (int q = 0; q < XN; q++) {
-                const float2 t = make_float2(__shfl_xor_sync(0xffffffffu, x[q].x, TC),
-                                             __shfl_xor_sync(0xffffffffu, x[q].y, TC));
+                const float2 t = make_float2(__shfl_xor_sync(0xffffffffu, x[q].x, S::PD * TC),
+                                             __shfl_xor_sync(0xffffffffu, x[q].y, S::PD * TC));
                 x[q] = csgn_add(sgn, x[q], t);  // x[q] + x[q + A/2] (even half) or their difference
             }
 #pragma unroll
@@ -373,15 +386,18 @@ struct LineCtx {
 #pragma unroll
             for (int q = 0; q < XN; q++) {
                 const int j = xpos(q);
-                float2 nv = cscale(x[q], rd(c[1] + j));
+                // staged tables: the padded index (positions >= L/2 are the odd pair halves, or the
+                // upper values of a thread)
+                const int jc = j + (S::STAGE ? 2 * upper(q) : 0);
+                float2 nv = cscale(x[q], rd(c[1] + jc));
                 if (!no_old) {
-                    const float d = rd(c[0] + j);
+                    const float d = rd(c[0] + jc);
                     const float2 o = pf[j * TC + cl];
                     nv.x = fmaf(d, o.x, nv.x);
                     nv.y = fmaf(d, o.y, nv.y);
                 }
                 st[sidx(q)] = nv;
-                x[q] = c[2] ? cscale(nv, rd(c[2] + j)) : nv;
+                x[q] = c[2] ? cscale(nv, rd(c[2] + jc)) : nv;
             }
         }
     }
@@ -436,8 +452,8 @@ struct LineCtx {
 #pragma unroll
         for (int i = 0; i < 3; i++) {
             d[i] = dsrc[i] ? tab2 + (2 + i) * L : nullptr;
-            c1[i] = a.c1[i] ? tab1 + i * L : nullptr;
-            c2[i] = a.c2[i] ? tab1 + (3 + i) * L : nullptr;
+            c1[i] = a.c1[i] ? tab1 + i * S::CSTR : nullptr;
+            c2[i] = a.c2[i] ? tab1 + (3 + i) * S::CSTR : nullptr;
         }
         ti = tab2 + r;
         tf = tab2 + L + r;
@@ -573,6 +589,7 @@ LineKernels make_line_kernels() {
     k.ra = S::A;
     k.rb = S::B;
     k.pair = S::PAIR;
+    k.pnew = S::PNEW;
     return k;
 }
 

@@ -326,3 +326,45 @@ def test_c4_workload_forward_and_adjoint_match_oracle_reduced_T(oracle_mod, dev)
     y = np.random.default_rng(16).standard_normal((g.T, s.m))
     assert rel(gpu_adjoint(op, y, dev), oracle_mod.adjoint(g, s, y)) < TOL
     op.close()
+
+
+# ------------------------------------------------------------------------------ largest grid
+
+def test_largest_grid_without_pml_matches_exact_solution(oracle_mod, dev):
+    """256x256x256, every axis at the longest supported line (z lines included, whose output
+    prefetch shares the state-1 tile at this length), PML off: sampled time steps of the full-plane
+    forward against p^n = F^-1[cos(n c |k| dt) F p0] (oracle FFT), and the FP32 dot test."""
+    g = presets.Grid(256, 256, 256, dx=50e-6, T=40, pml_size=0, sensor_z=128)
+    p0 = synth.gaussian_balls(g.shape, 6, 3.0, 21, pml=80)
+    op = make_op(g, full(g))
+    f = gpu_forward(op, p0, dev).reshape(g.T, g.ny, g.nx)
+    P0 = oracle_mod.fft3(p0.astype(np.complex128))
+    ks = [np.array([oracle_mod.wavenumber(m, n, g.dx) for m in range(n)]) for n in g.shape]
+    K = np.sqrt(ks[0][:, None, None] ** 2 + ks[1][None, :, None] ** 2 + ks[2][None, None, :] ** 2)
+    steps = (1, 20, 39)
+    ref = np.stack([oracle_mod.fft3(P0 * np.cos(n * g.c * K * g.dt), inverse=True).real[g.sensor_z]
+                    for n in steps])
+    assert np.linalg.norm(ref) > 1e-3 * np.linalg.norm(p0[g.sensor_z])
+    assert rel(f[list(steps)], ref) < TOL
+    y = np.random.default_rng(22).standard_normal((g.T, g.m_plane))
+    Aty = gpu_adjoint(op, y, dev)
+    lhs, rhs = np.sum(f.ravel() * y.ravel()), np.sum(p0.ravel() * Aty.ravel())
+    assert abs(lhs - rhs) / (np.linalg.norm(f) * np.linalg.norm(y)) < 1e-5
+    op.close()
+
+
+@pytest.mark.slow
+def test_largest_grid_matches_oracle_reduced_T(oracle_mod, dev):
+    """256x256x256 with a 10-voxel PML, T = 6, the full detection plane through the strongest source
+    (so every recorded step carries signal): forward and adjoint against the FP64 oracle."""
+    shape = (256, 256, 256)
+    p0 = synth.gaussian_balls(shape, 4, 3.0, 23, pml=12)
+    zs = int(np.argmax(np.linalg.norm(p0.reshape(shape[0], -1), axis=1)))
+    g = presets.Grid(*shape, dx=50e-6, T=6, pml_size=10, sensor_z=zs)
+    op = make_op(g, full(g))
+    f_ref = oracle_mod.forward(g, full(g), p0)
+    assert np.linalg.norm(f_ref) > 0.1 * np.linalg.norm(p0[zs])
+    assert rel(gpu_forward(op, p0, dev), f_ref) < TOL
+    y = np.random.default_rng(24).standard_normal((g.T, g.m_plane))
+    assert rel(gpu_adjoint(op, y, dev), oracle_mod.adjoint(g, full(g), y)) < TOL
+    op.close()

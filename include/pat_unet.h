@@ -3,7 +3,7 @@
  * (4 levels, 16/32/64/128 channels) that maps the back-projection A^T C^T f to a starting image,
  * trained on phantoms paired with their own TV-Bregman reconstructions.  The paper has no learned
  * component; the solver it warm-starts is Sec. 4.5-4.6 (TV+ with Bregman iterations, App. B), which
- * stays the fallback and the judge of the warm start's error.
+ * stays the fallback and the reference the warm start's error is measured against.
  *
  * Conventions (in addition to those of pat.h):
  *   Activations are channels-last BF16 tensors [V][ld] (V = D*H*W voxels, z slowest, x fastest);

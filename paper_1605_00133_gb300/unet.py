@@ -1,6 +1,6 @@
 """Learned warm start for the TV-Bregman solver: a 3D U-Net that maps the back-projection A^T C^T f
 to a starting image (the paper has no learned component; the solver it warm-starts is Sec. 4.5-4.6
-and App. B, and stays the fallback and the judge of the warm start's error).
+and App. B, and stays the fallback and the reference the warm start's error is measured against).
 
 Architecture: 4 levels with 16/32/64/128 channels, two 3x3x3 convolutions + ReLU per level and
 side, 2x2x2 average pooling down, nearest-neighbour upsampling and channel concatenation

@@ -46,7 +46,7 @@ typedef enum {
     PAT_ERR_INVALID_ARG = 1,   /* bad pointer, size, descriptor or index set */
     PAT_ERR_CUDA = 2,          /* a CUDA runtime call or kernel launch failed */
     PAT_ERR_OOM = 3,           /* device workspace could not be allocated */
-    PAT_ERR_TIMEOUT = 4,       /* reserved: a bounded device-side wait gave up */
+    PAT_ERR_TIMEOUT = 4,       /* a bounded device-side wait gave up (pat_device_status) */
     PAT_ERR_NOT_CONVERGED = 5, /* reserved for iterative solvers */
     PAT_ERR_UNSUPPORTED = 6    /* valid request this build does not handle (e.g. grid too large) */
 } pat_status;
@@ -197,6 +197,14 @@ pat_status pat_bregman_solve(pat_grid* grid, const float* f_dev, const float* wa
 pat_status pat_profile_enable(pat_grid* grid, int32_t enable);
 pat_status pat_profile_read(pat_grid* grid, int32_t max_classes, char* names, double* total_ms,
                             int64_t* launches, int32_t* n_classes);
+
+/* Device-side status of the grid's time-stepping kernels.  They stage their inputs with bulk
+ * asynchronous copies and bound every wait for one (about a second); a wait that gives up is
+ * recorded in a device word of the grid instead of hanging the GPU, and the results of the calls
+ * since then are undefined.  Synchronises cuda_stream, then reads and clears the record: PAT_OK, or
+ * PAT_ERR_TIMEOUT with pat_last_error() naming the copies that never landed.  pat_forward and
+ * pat_adjoint do not synchronise, so they cannot report this themselves. */
+pat_status pat_device_status(pat_grid* grid, void* cuda_stream);
 
 /* Message for the last failed call on this thread ("" if none). Valid until the next call. */
 const char* pat_last_error(void);

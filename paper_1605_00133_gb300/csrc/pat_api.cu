@@ -226,6 +226,7 @@ pat_status build_tables(pat_grid* G) {
             if ((st = upload(G, &G->t.kappa[a], kap, "kappa")) != PAT_OK) return st;
         }
     }
+    if ((st = upload(G, &G->t.err, std::vector<int32_t>(1, 0), "device status word")) != PAT_OK) return st;
     // PML-derived coefficient tables, and the per-pass table blocks
     for (int a = 0; a < 3; a++) {
         std::vector<std::vector<float>> ct(CT_COUNT, std::vector<float>(n[a]));
@@ -497,6 +498,27 @@ pat_status pat_get_indices(const pat_grid* G, int32_t* host_idx_or_perm, int32_t
     }
     if (e != cudaSuccess) return cuda_fail(e, "pat_get_indices");
     return PAT_OK;
+}
+
+pat_status pat_device_status(pat_grid* G, void* stream) {
+    g_err.clear();
+    if (!G) return fail(PAT_ERR_INVALID_ARG, "pat_device_status: NULL grid");
+    pat_status st = check_device(G);
+    if (st != PAT_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    int32_t word = 0;
+    cudaError_t e = cudaMemcpyAsync(&word, G->t.err, sizeof(word), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "pat_device_status");
+    if (word == 0) return PAT_OK;
+    e = cudaMemsetAsync(G->t.err, 0, sizeof(int32_t), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "pat_device_status: clear");
+    std::string what;
+    if (word & 1) what += " table block";
+    if (word & 2) what += " state-1 tile";
+    if (word & 4) what += " state-2 tile";
+    return fail(PAT_ERR_TIMEOUT, "pat_device_status: a line pass gave up waiting for its bulk copy of the" + what);
 }
 
 pat_status pat_profile_enable(pat_grid* G, int32_t enable) {

@@ -229,6 +229,40 @@ __device__ __forceinline__ float ldg_stream(const float* p) {
     return v;
 }
 
+// Bulk asynchronous copies (the TMA unit's non-tensor form): one thread copies a contiguous block of
+// global memory into this CTA's shared memory; the copy completes on an mbarrier, whose phase
+// completion makes the data visible to every thread that waits on it.  Addresses 16-byte aligned,
+// size a multiple of 16.
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+// make initialised mbarriers visible to the asynchronous proxy (before the first copy uses them)
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+// the single arrival of a phase, announcing `bytes` of copies that complete it
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_addr(dst)), "l"(src), "r"(bytes), "r"(smem_addr(bar)) : "memory");
+}
+// Wait for phase `parity` of an mbarrier to complete: each poll suspends the thread for at most about
+// a microsecond, and after `polls` polls (about a second for 1 << 20) the wait gives up and returns
+// false; the caller records the failure and carries on, so no thread is left waiting.
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, int polls) {
+    for (int i = 0; i < polls; i++) {
+        unsigned done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done) : "r"(smem_addr(bar)), "r"(parity), "r"(1000u) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
 // Asynchronous global -> shared copies (cp.async): the data land in shared memory without passing
 // through registers; a thread may read what it copied itself after cp_async_wait<N>() (at most N of
 // its committed groups still pending), other threads only after a barrier on top of that.

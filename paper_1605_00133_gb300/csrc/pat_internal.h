@@ -77,6 +77,7 @@ struct DeviceTables {
     // then the coefficient tables of state 1 and state 2 (len + 2 floats each, entry j at
     // j + 2 [j >= len/2])
     float2* pass[PS_COUNT][3];
+    int* err;                   // one word: bulk copies of the line passes that never landed (bits)
 };
 
 // Mixed representation: the split fields u_i, rho_i of axis i are kept with axis i in real space

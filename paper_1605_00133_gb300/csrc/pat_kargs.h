@@ -86,6 +86,7 @@ struct LineArgs {
     const float* c1[3];         // state 1: decay, input gain, output gain (one entry per position)
     const float* c2[3];         // state 2
     const float2* tabs;         // LM_STEP: all the tables above in one block (DeviceTables::pass)
+    int* err;                   // device word: bit i set when bulk copy i of a pass never landed
     float2* rec;                // z lines: plane spectrum recorded this step (LF_RECORD) ...
     const float2* inj;          // ... or injected this step (LF_INJECT); batch stride plane_bs
     long long plane_bs;

@@ -89,7 +89,17 @@ struct LS {
     static constexpr int TAB1 = STAGE ? 6 * CSTR : 0;
     static constexpr size_t SBASE = (2 * (size_t)BUF + TAB2) * sizeof(float2) + TAB1 * sizeof(float);
     static constexpr bool PFO_ALIAS = (int)(SMEM_SM / (SBASE + 3 * (size_t)TILE * sizeof(float2) + 1024)) < MINB_T;
-    static constexpr size_t smem = SBASE + (PFO_ALIAS ? 2 : 3) * (size_t)TILE * sizeof(float2);
+    static constexpr size_t BAR_OFF = SBASE + (PFO_ALIAS ? 2 : 3) * (size_t)TILE * sizeof(float2);
+    static constexpr size_t smem = BAR_OFF + 32;  // three mbarriers (tables, state 1, state 2)
+    static constexpr unsigned TILE_BYTES = TILE * sizeof(float2);
+    // old state tiles staged by bulk copies (TMA) up to 8 KB, in BULK_PARTS pieces; larger tiles by
+    // per-thread 16-byte cp.async copies
+    static constexpr bool BULK = TILE_BYTES <= 8192;
+    static constexpr int BULK_PARTS = 1;
+    static constexpr unsigned TAB_BYTES = TAB2 * sizeof(float2) + TAB1 * sizeof(float);
+    static_assert(BAR_OFF % 16 == 0 && TILE_BYTES % 16 == 0 && TAB_BYTES % 16 == 0 &&
+                      (2 * (size_t)BUF * sizeof(float2)) % 16 == 0,
+                  "bulk copies need 16-byte aligned shared-memory blocks and sizes");
     static constexpr int MINB_S = (int)(SMEM_SM / (smem + 1024));
     static constexpr int MINB = (MINB_T < MINB_S) ? MINB_T : (MINB_S > 0 ? MINB_S : 1);
     // exchange rows are swizzled (bit 0 of the row flipped by bit 0 of row / B) when a row is only
@@ -131,6 +141,7 @@ struct LineCtx {
     const float2* tf;
     float2* tab2;      // shared copies (S::STAGE): twi, twf, k-space factors [3]
     float* tab1;       // ... state coefficients [2][3]
+    unsigned long long* bar;  // mbarriers of the bulk copies: tables, state 1, state 2
     int ka, kb;     // x lines: kz, ky
     int ma, mb;     // x lines: the mirror line's kz, ky
 
@@ -142,6 +153,7 @@ struct LineCtx {
         pfo = S::PFO_ALIAS ? pf1 : pf2 + S::TILE;
         tab2 = pf2 + (S::PFO_ALIAS ? 1 : 2) * S::TILE;
         tab1 = reinterpret_cast<float*>(tab2 + S::TAB2);
+        bar = reinterpret_cast<unsigned long long*>(reinterpret_cast<char*>(smem) + S::BAR_OFF);
         const int tid = threadIdx.x;
         cl = tid % TC;
         r = tid / TC;
@@ -402,9 +414,36 @@ struct LineCtx {
         }
     }
 
-    // issue the cp.async copy of one old state tile (one commit group; every thread commits it).
-    // The tile is one contiguous block (padding lines included) copied in 16-byte chunks, so a
-    // thread's copies are not the values it later reads: consumers wait, then pass a barrier.
+    // Bulk copies of a STEP pass's inputs into shared memory, issued by thread 0 as the kernel
+    // starts: the table block (S::STAGE), and the old tiles of state 1 and state 2 (each one
+    // contiguous block of the tile-major layout, padding lines included).  Each completes on its own
+    // mbarrier; the barrier initialisation is published by a __syncthreads before any thread waits.
+    __device__ __forceinline__ void issue_copies(bool old1, bool old2) const {
+        if (threadIdx.x != 0) return;
+        mbar_init(bar + 0, 1);
+        mbar_init(bar + 1, 1);
+        mbar_init(bar + 2, 1);
+        mbar_fence_init();
+        if (S::STAGE) {
+            mbar_arrive_expect_tx(bar + 0, S::TAB_BYTES);
+            bulk_copy_g2s(tab2, a.tabs, S::TAB_BYTES, bar + 0);
+        }
+        constexpr unsigned PART = S::TILE_BYTES / S::BULK_PARTS;
+        constexpr int PART2 = (int)(PART / sizeof(float2));
+        static_assert(PART % 16 == 0, "bulk copy pieces of 16-byte multiples");
+        if (S::BULK && old1) {
+            mbar_arrive_expect_tx(bar + 1, S::TILE_BYTES);
+            for (int i = 0; i < S::BULK_PARTS; i++)
+                bulk_copy_g2s(pf1 + i * PART2, a.st1 + tbase + i * PART2, PART, bar + 1);
+        }
+        if (S::BULK && old2) {
+            mbar_arrive_expect_tx(bar + 2, S::TILE_BYTES);
+            for (int i = 0; i < S::BULK_PARTS; i++)
+                bulk_copy_g2s(pf2 + i * PART2, a.st2 + tbase + i * PART2, PART, bar + 2);
+        }
+    }
+    // without bulk copies (!S::BULK): every thread's share of one old state tile as 16-byte cp.async
+    // copies (one commit group, committed by every thread; read after a wait and a barrier)
     __device__ __forceinline__ void prefetch(const float2* __restrict__ st, float2* pf, bool on) const {
         constexpr int NCH = L * (TC / 2);  // 16-byte chunks per tile
         static_assert(NCH % S::NT == 0, "tile chunks per thread");
@@ -417,6 +456,10 @@ struct LineCtx {
             }
         }
         cp_async_commit();
+    }
+    // wait for bulk copy i (bounded; a copy that never lands is recorded in a.err, bit i)
+    __device__ __forceinline__ void wait_copy(int i) const {
+        if (!mbar_wait(bar + i, 0, 1 << 20)) atomicOr(a.err, 1 << i);
     }
 
     // cp.async copy of the old output of z and y lines into pfo (one commit group, committed by every
@@ -439,15 +482,10 @@ struct LineCtx {
         cp_async_commit();
     }
 
-    // Copy the pass's table block (a.tabs: twi, twf, three k-space factors, six coefficient tables)
-    // to shared memory (one cp.async group, committed by every thread) and point ti/tf at the copies;
-    // d and c1, c2 receive the shared copies of a's factor and coefficient tables (NULL stays NULL).
-    // The copies are read after a wait and a barrier.
+    // Point ti/tf at the shared copy of the pass's table block (a.tabs: twi, twf, three k-space
+    // factors, six coefficient tables; bulk copy 0); d and c1, c2 receive the shared copies of a's
+    // factor and coefficient tables (NULL stays NULL).
     __device__ __forceinline__ void stage(const float2** d, const float** c1, const float** c2) {
-        constexpr int NCH = (S::TAB2 * (int)sizeof(float2) + S::TAB1 * (int)sizeof(float)) / 16;
-#pragma unroll
-        for (int q = threadIdx.x; q < NCH; q += S::NT) cp_async16(tab2 + 2 * q, a.tabs + 2 * q);
-        cp_async_commit();
         const float2* dsrc[3] = {a.dpre, a.dmid, a.dpost};
 #pragma unroll
         for (int i = 0; i < 3; i++) {
@@ -502,10 +540,14 @@ __global__ void __launch_bounds__(LS<L>::NT, LS<L>::MINB) line_pass_kernel(LineA
     const float2* dk[3] = {a.dpre, a.dmid, a.dpost};
     const float* c1[3] = {a.c1[0], a.c1[1], a.c1[2]};
     const float* c2[3] = {a.c2[0], a.c2[1], a.c2[2]};
+    const bool old1 = (a.flags & LF_NO_OLD1) == 0, old2 = (a.flags & LF_NO_OLD2) == 0;
     if (a.mode == LM_STEP) {
+        c.issue_copies(old1, old2);
+        if (!S::BULK) {
+            c.prefetch(a.st1, c.pf1, old1);
+            c.prefetch(a.st2, c.pf2, old2);
+        }
         if (S::STAGE) c.stage(dk, c1, c2);
-        c.prefetch(a.st1, c.pf1, (a.flags & LF_NO_OLD1) == 0);
-        c.prefetch(a.st2, c.pf2, (a.flags & LF_NO_OLD2) == 0);
         const float* kp = a.kap + (size_t)blockIdx.x * (L * S::TC) + c.r * S::TC + c.cl;
 #pragma unroll
         for (int k2 = 0; k2 < B; k2++) kap[k2] = c.vcol ? ldg_stream(kp + k2 * A * S::TC) : 0.f;
@@ -522,24 +564,28 @@ __global__ void __launch_bounds__(LS<L>::NT, LS<L>::MINB) line_pass_kernel(LineA
         return;
     }
 
-    if (S::STAGE) {
-        cp_async_wait<2>();  // the tables have landed (the states may still be in flight)
-        __syncthreads();
-    }
+    __syncthreads();  // publishes the mbarrier initialisation
+    if (S::STAGE) c.wait_copy(0);  // the tables
     c.factor(v, dk[0], kap, a.s_pre);
-    cp_async_wait<1>();  // state 1 has landed; the barrier inside inv() publishes it to every thread
+    if (!S::BULK) cp_async_wait<1>();  // state 1 has landed; the barrier inside inv() publishes it
     c.inv(v, x, c.buf0);
-    c.update(a.st1, c1, (a.flags & LF_NO_OLD1) != 0, c.pf1, x);
+    if (S::BULK && old1) c.wait_copy(1);  // the old state 1
+    c.update(a.st1, c1, !old1, c.pf1, x);
     if (late) pdl_wait();  // the new spectrum is written by the preceding pass
     if (a.flags & LF_TRIGGER_MID) pdl_trigger();
     const bool pre = accum && AX != 2;
-    if (S::PFO_ALIAS && pre) __syncthreads();  // every thread's state-1 update has read pf1
+    if (S::PFO_ALIAS && pre) {
+        // every thread's state-1 update has read pf1 (written by the bulk copy) before it is reused
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+    }
     c.prefetch_out(pre);
     c.fwd(x, v, c.buf1);
     c.factor(v, dk[1], kap, a.s_mid);
-    cp_async_wait<1>();  // state 2 likewise (the old output may still be in flight)
+    if (!S::BULK) cp_async_wait<1>();  // state 2 likewise (the old output may still be in flight)
     c.inv(v, x, c.buf0);
-    c.update(a.st2, c2, (a.flags & LF_NO_OLD2) != 0, c.pf2, x);
+    if (S::BULK && old2) c.wait_copy(2);  // the old state 2
+    c.update(a.st2, c2, !old2, c.pf2, x);
     cp_async_wait<0>();  // old output; published by the barrier inside fwd()
     c.fwd(x, v, c.buf1);
     c.factor(v, dk[2], kap, a.s_post);

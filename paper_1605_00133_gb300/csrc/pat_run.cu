@@ -199,6 +199,7 @@ static LineArgs line_base(const Geom& g, const DeviceTables& t, const Workspace&
     a.g = g;
     a.ncols = g.ncols[ax];
     a.tw = t.tw[ax];
+    a.err = t.err;
     a.twi = t.twi[ax];
     a.twf = t.twf[ax];
     a.st1 = w.ms[ax][0];

@@ -158,6 +158,13 @@ class PatOperator:
                "residuals": [R.residual[i] for i in range(R.n_residual)]}
         return out, rep
 
+    # ------------------------------------------------------------------ device status
+    def device_status(self, device=None) -> None:
+        """Raise if a bounded device-side wait of this grid's kernels gave up since the last check
+        (see pat_device_status); synchronises the current stream of `device`."""
+        dev = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+        _lib.check(_lib.load().pat_device_status(self._h, _stream_ptr(dev)))
+
     # ------------------------------------------------------------------ kernel timing
     def profile(self, enable: bool = True) -> None:
         """Bracket every kernel launch with CUDA events (see pat_profile_enable)."""

@@ -368,3 +368,17 @@ def test_largest_grid_matches_oracle_reduced_T(oracle_mod, dev):
     y = np.random.default_rng(24).standard_normal((g.T, g.m_plane))
     assert rel(gpu_adjoint(op, y, dev), oracle_mod.adjoint(g, full(g), y)) < TOL
     op.close()
+
+
+def test_device_status_is_clean_after_forward_and_adjoint(dev):
+    """The line passes' bounded waits for their bulk copies never give up in normal operation:
+    pat_device_status reports PAT_OK after forward and adjoint calls, batched and with every
+    line length of the small-grid cases (sampling, PML and the long-line tile sharing included)."""
+    for shape in [(8, 8, 8), (16, 64, 128), (8, 256, 16), (256, 8, 8)]:
+        g = presets.Grid(*shape, dx=100e-6, T=12, pml_size=2, batch=2)
+        op = make_op(g, full(g))
+        x = torch.rand((2,) + g.shape, dtype=torch.float32, device=dev)
+        y = op.forward(x)
+        op.adjoint(y)
+        op.device_status(dev)
+        op.close()

@@ -24,18 +24,21 @@
 //
 // A CTA owns TC lines.  A line's length-L transform is the two-pass split of pat_fft.cuh: in the
 // k-space layout thread r < A holds X[r + A k2] (k2 < B), in the spatial layout thread r < B holds
-// x[r + B k2] (k2 < A) -- or, when A = 2B, the thread pair (2 r', 2 r' + 1) shares row group r'
-// (each holds A/2 of its values and computes half of its A-point DFT); each transform is one
-// exchange through shared memory laid out [row][line] with the line index fastest.  Two exchange buffers alternate, so every transform costs one
-// barrier.  The old values of both states are copied to shared memory with cp.async as soon as the
-// kernel starts, and the old values of the spectrum a y or z pass adds to as soon as its writer has
-// completed, so their latency overlaps transforms instead of stalling each update.
+// x[r + B k2] (k2 < A) -- or, when A = 2B, a thread pair shares row group xr (each half holds A/2 of
+// its values and computes half of its A-point DFT; LS::PNEW says which rows pair up); each transform
+// is one exchange through shared memory laid out [row][line] with the line index fastest.  Two
+// exchange buffers alternate, so every transform costs one barrier.  The pass's table block and the
+// old values of both states are copied to shared memory as soon as the kernel starts (bulk copies of
+// the TMA unit completing on mbarriers, or per-thread cp.async for 16 KB tiles), and the old values
+// of the spectrum a y or z pass adds to as soon as its writer has completed, so their latency
+// overlaps transforms instead of stalling each update.
 //
 // Launch overlap.  The y and z passes of a step read only the previous step's spectrum and their own
 // states until they add to the new spectrum, so they are launched as programmatic dependents that
 // start at once and wait for their predecessor (griddepcontrol.wait) only after their first state
-// update, before fetching the spectrum they add to (LF_LATE_WAIT).  Everything they read before the wait was written by kernels that had completed
-// before the x pass of the step passed its own wait, and is read through L2 (ld.cg, cp.async.cg).
+// update, before fetching the spectrum they add to (LF_LATE_WAIT).  Everything they read before the
+// wait was written by kernels that had completed before the x pass of the step passed its own wait,
+// and is read through L2 (ld.cg, cp.async.cg, bulk copies).
 // No kernel waits on a grid whose CTAs have not all started, so the overlap cannot deadlock.
 //
 // States and kappa are stored tile-major, [B][tile][L][TC] (tile = line / TC, lines padded to a

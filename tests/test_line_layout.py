@@ -1,7 +1,7 @@
 """Host-side model of the line pass's shared-memory index arithmetic (pat_line.cuh), no GPU.
 
 The kernel writes every exchange-buffer address as a per-thread base plus a compile-time offset,
-resolving the bank swizzle per thread.  This test restates, for the CTA shapes the c2 and c4 grids use,
+resolving the bank swizzle per thread.  This test restates, for the CTA shape of every instantiated line length,
 (a) the thread -> (line, row, pair half) mapping, (b) the generic swizzle (bit 0 of a row flipped by
 bit 0 of row / B, and also of row / A when pairs are rows r and r + 2), (c) the per-thread row formulas
 of the four exchange accesses, and checks that (c) equals (b) applied to the plain row, that the
@@ -125,7 +125,7 @@ def worst_conflict(width, addrs):
     return worst
 
 
-SHAPES = [shape(L) for L in (64, 128, 256)]
+SHAPES = [shape(L) for L in (8, 16, 32, 64, 128, 256)]  # every instantiated line length
 
 
 @pytest.mark.parametrize("s", SHAPES, ids=[f"L{s['L']}" for s in SHAPES])

@@ -1,12 +1,12 @@
 """Host-side model of the line pass's shared-memory index arithmetic (pat_line.cuh), no GPU.
 
 The kernel writes every exchange-buffer address as a per-thread base plus a compile-time offset,
-resolving the bank swizzle per thread.  This test restates, for the CTA shape of every instantiated line length,
-(a) the thread -> (line, row, pair half) mapping, (b) the generic swizzle (bit 0 of a row flipped by
-bit 0 of row / B, and also of row / A when pairs are rows r and r + 2), (c) the per-thread row formulas
-of the four exchange accesses, and checks that (c) equals (b) applied to the plain row, that the
-swizzle permutes the rows, that pair partners sit in the same warp at the shuffle distance, and that
-the exchange, state-tile and staged-table reads are free of bank conflicts.
+resolving the bank swizzle per thread.  This test restates, for the CTA shape of every instantiated
+line length, (a) the thread -> (line, row, pair half) mapping, (b) the generic swizzle (bit 0 of a row
+flipped by bit 0 of row / B, and also of row / A when pairs are rows r and r + 2), (c) the per-thread
+row formulas of the four exchange accesses, and checks that (c) equals (b) applied to the plain row,
+that the swizzle permutes the rows, that pair partners sit in the same warp at the shuffle distance,
+and that the exchange, state-tile and staged-table reads are free of bank conflicts.
 """
 import pytest
 

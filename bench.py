@@ -8,7 +8,11 @@ plus one adjoint (f -> A^T C^T f) on each of `--batch` independent volumes, inpu
 GPU.  Between steps a 256 MiB buffer is written (inside the timed region) so that no step starts
 with the previous step's data in the 129 MB L2.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B] [--workload c2]
+The metric's second half (the `solve` object, on by default at batch 1): one TV-Bregman
+reconstruction with the workload's schedule (seconds, reconstructions per minute) and the plain
+solve's time to 2 % relative error against a converged reconstruction.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--batch B] [--workload c2] [--no-solve]
     python bench.py --impl reference ...   # the FP64 CPU oracle on the host cores, same metric
 
 Multi-GPU: replicas only (torchrun, one rank per GPU, independent volumes, no collective on the
@@ -46,8 +50,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--solve", action="store_true",
-                    help="also time one TV-Bregman reconstruction of the workload (reported, not the metric)")
+    ap.add_argument("--no-solve", action="store_true",
+                    help="skip the TV-Bregman reconstruction timing (the `solve` object)")
     ap.add_argument("--warm", action="store_true",
                     help="also train the learned warm start and time warm vs plain solves to 2 %% error")
     ap.add_argument("--warm-train", type=int, default=64)
@@ -150,7 +154,7 @@ def run_reference(args):
     from paper_1605_00133_gb300 import presets
     oracle.build()
     w = presets.workload(args.workload)
-    Ts = 4
+    Ts = 24  # 23 time steps each way: the per-call set-up is under 5 % of a sample
     for _ in range(args.warmup):
         oracle_pairs_per_s(w, Ts)
     tot = 0.0
@@ -167,7 +171,7 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": workload_config(w, 1),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, "cpu_model": cpu_model(), "nproc": os.cpu_count()},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -241,6 +245,7 @@ def main():
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
     clk = clocks.stop()
+    op.device_status(dev)  # raises if a bounded device-side wait gave up (results invalid)
     barrier()
     ms = max_over_ranks(ms)
     pairs = B * world * args.steps
@@ -253,11 +258,15 @@ def main():
         step()
     prof = op.profile_read()
     op.profile(False)
+    op.device_status(dev)
     total_prof = sum(v[0] for v in prof.values())
     launches_per_step = sum(v[1] for v in prof.values()) / args.steps
     kernels = {k: {"ms_total": v[0], "launches": v[1], "avg_us": 1e3 * v[0] / v[1],
                    "share": v[0] / total_prof} for k, v in prof.items()}
-    dominant = max(kernels, key=lambda k: kernels[k]["ms_total"])
+    kernels["note"] = ("serialised run: the same steps again with every launch bracketed by CUDA events, "
+                       "which removes the overlap of successive launches; per-launch times and shares of "
+                       "that run, not a decomposition of ms_per_step")
+    dominant = max((k for k in kernels if k != "note"), key=lambda k: kernels[k]["ms_total"])
 
     # roofline: the time step is the unit of work (48 bytes per voxel per step: six FP32 state fields
     # read and written once); one step = 3 line-pass launches (x, y, z) on one stream
@@ -272,7 +281,7 @@ def main():
     bytes_per_step = 48.0 * g.n * B
     achieved = bytes_per_step / step_s / 1e9
     # DRAM bytes of one forward time step from the committed ncu capture, valid only for the kernel
-    # sources it was taken on (profiles/pat_line_pass_c2.md)
+    # sources it was taken on
     traffic = STEP_TRAFFIC.get((_source_hash(), w.name, B))
     roofline = {"bound": "hbm", "kernel": "time step (line passes x, y, z of A, and of A^T)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
@@ -281,17 +290,18 @@ def main():
                 "dominant_kernel": dominant, "dominant_share": kernels[dominant]["share"],
                 "dominant_avg_us": kernels[dominant]["avg_us"]}
 
-    # second roofline: the conventional scheme's algorithmic flops, ten real 3D FFTs
-    # (2.5 N log2 N each) plus ~60 N pointwise per time step, against the FP32 FMA peak of the CUDA
-    # cores from unit counts and clock (152 SMs x 128 lanes x 2 flops x max SM clock)
-    import math
-    flops_per_step = 10 * 2.5 * g.n * math.log2(g.n) + 60.0 * g.n
+    # second roofline: the FP32 arithmetic this method executes per time step, against the FP32 FMA
+    # peak of the CUDA cores from unit counts and clock (152 SMs x 128 lanes x 2 flops x max SM clock)
+    flops_per_step = method_flops_per_step(g)
     sm_mhz = clk.get("sm_max_mhz") or 2070.0
     alu_peak = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
     alu_achieved = flops_per_step * B / step_s / 1e12
     roofline_alu = {"bound": "alu", "achieved": alu_achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                    "frac": alu_achieved / alu_peak,
-                    "algorithmic_flops_per_unit": "10 x 2.5 N log2 N + 60 N per time step",
+                    "frac": alu_achieved / alu_peak, "flops_per_unit": flops_per_step,
+                    "algorithmic_flops_per_unit": ("per time step, per axis i: 4 complex line transforms "
+                                                   "(5 L_i log2 L_i flops each) on the axis's lines, and "
+                                                   "38 flops per line point (three k-space factors, two "
+                                                   "state updates, the accumulation)"),
                     "peak_source": "152 SMs x 128 FP32 lanes x 2 x max SM clock"}
 
     # end to end through the public API: pinned host p0 -> device, A, A^T, device -> pinned host
@@ -316,44 +326,15 @@ def main():
             step_e2e()
         e1.record()
         torch.cuda.synchronize()
+        op.device_status(dev)
         ms_e2e = max_over_ranks(e0.elapsed_time(e1))
         e2e = {"value": pairs / (ms_e2e / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": int(p0_h.numel() * 4), "d2h_bytes_per_step": int(p_h.numel() * 4)}
 
     solve = None
-    if args.solve and B == 1:
-        # one TV+Br reconstruction (outer x inner FISTA steps, each one A + A^T pair plus restarts),
-        # then the plain solve's time to 2 % relative error against its own final image: the solves
-        # with k = 1, 2, ... Bregman steps (deterministic, so solve k ends at the k-th iterate of the
-        # full solve), each timed from scratch
-        from paper_1605_00133_gb300.presets import workload as _wl
-        wl = _wl(args.workload)
-        fnoisy = f + 0.01 * float(f.abs().max()) * torch.randn(f.shape, device=dev,
-                                                                generator=torch.Generator(device=dev).manual_seed(5))
-        lam = 2e-4
-
-        def timed_solve(outer):
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            pr, rp = op.bregman_solve(fnoisy, lam, outer=outer, inner=wl.inner, prox_iters=50, power_iters=20)
-            torch.cuda.synchronize()
-            return pr, rp, time.perf_counter() - t0
-
-        prec, rep, secs = timed_solve(wl.bregman_outer)
-        traj = []
-        for k in range(1, wl.bregman_outer):
-            pk, _, tk = timed_solve(k)
-            traj.append({"bregman_steps": k, "seconds": tk,
-                         "rel_err_vs_final": float((pk - prec).norm() / prec.norm())})
-        traj.append({"bregman_steps": wl.bregman_outer, "seconds": secs, "rel_err_vs_final": 0.0})
-        t2 = next(t["seconds"] for t in traj if t["rel_err_vs_final"] <= 0.02)
-        solve = {"seconds": secs, "reconstructions_per_min": 60.0 / secs, "outer": wl.bregman_outer,
-                 "inner": wl.inner, "prox_iters": 50, "lambda": lam, "power_iters": 20,
-                 "fista_iterations": rep["inner_total"], "restarts": rep["restarts"],
-                 "residuals": rep["residuals"], "rel_err_vs_phantom": float((prec - p0).norm() / p0.norm()),
-                 "plain_seconds_to_2pct": t2, "trajectory": traj,
-                 "warm_start": "plain cold-start solve; --warm trains the learned U-Net warm start and "
-                               "times warm against plain (the line's warm_start object)"}
+    if not args.no_solve and B == 1:
+        solve = solve_experiment(args, op, f, p0, dev)
+        op.device_status(dev)
 
     warm = None
     if args.warm and B == 1:
@@ -361,11 +342,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        Ts = 100
-        v, t, threads = oracle_pairs_per_s(w, Ts)
-        cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
-               "sample": (f"one oracle A + A^T on the full {g.nz}x{g.ny}x{g.nx} grid with T = {Ts} "
-                          f"({Ts - 1} time steps each way, {t:.1f} s), scaled to T = {g.T}")}
+        cpu = cpu_baseline(w)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -383,6 +360,138 @@ def main():
     if dist:
         dist.destroy_process_group()
     return 0
+
+
+def method_flops_per_step(g):
+    """FP32 flops of one time step of the mixed-representation scheme: for each axis i, the lines of
+    that axis (the half spectrum's columns along it) take four complex length-L_i transforms
+    (5 L log2 L flops each, the radix-2 count) and 38 flops per line point (three complex k-space
+    factors at 8, two state updates at 6, the spectrum accumulation at 2)."""
+    import math
+    nzh, nxh = g.nz // 2 + 1, g.nx // 2 + 1
+    total = 0.0
+    for L, n_lines in ((g.nz, nxh * g.ny), (g.ny, g.nz * nxh), (g.nx, nzh * g.ny)):
+        total += n_lines * (4 * 5 * L * math.log2(L) + 38 * L)
+    return total
+
+
+def solve_experiment(args, op, f_clean, p0, dev):
+    """The metric's second half on the workload (noisy data: f + 1 % Gaussian noise).
+
+    * One TV-Bregman reconstruction with the workload's schedule (outer x inner FISTA steps, each one
+      A + A^T pair plus restarts; the step size from 20 power iterations inside the timed call):
+      seconds per reconstruction and reconstructions per minute.
+    * The plain solve's time to 2 % relative error against p_ref, a converged reconstruction (the
+      same solver, Bregman steps and prox iterations, 300 inner FISTA iterations per step, computed
+      once and not timed): solves with an increasing number of inner iterations per Bregman step,
+      each timed from scratch with the step size fixed, until one lands within 2 % of p_ref."""
+    import torch
+
+    from paper_1605_00133_gb300 import presets
+    wl = presets.workload(args.workload)
+    gen = torch.Generator(device=dev).manual_seed(5)
+    f = f_clean + 0.01 * float(f_clean.abs().max()) * torch.randn(f_clean.shape, device=dev, generator=gen)
+    lam, prox = 2e-4, 50
+
+    def timed(inner, L=0.0, prox_iters=prox):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pr, rp = op.bregman_solve(f, lam, outer=wl.bregman_outer, inner=inner, prox_iters=prox_iters, L=L,
+                                  power_iters=20)
+        torch.cuda.synchronize()
+        return pr, rp, time.perf_counter() - t0
+
+    prec, rep, secs = timed(wl.inner)
+    L = rep["L"]
+    p_ref, rref, t_ref = timed(300, L)
+    nref = float(p_ref.norm())
+    ladder = []
+    for inner in (10, 20, 50, 100, 150, 200):
+        pk, rk, tk = timed(inner, L)
+        ladder.append({"inner": inner, "seconds": tk, "fista_iterations": rk["inner_total"],
+                       "rel_err_vs_ref": float((pk - p_ref).norm()) / nref})
+        if ladder[-1]["rel_err_vs_ref"] <= 0.02:
+            break
+    t2 = next((e["seconds"] for e in ladder if e["rel_err_vs_ref"] <= 0.02), None)
+    return {"seconds": secs, "reconstructions_per_min": 60.0 / secs, "outer": wl.bregman_outer,
+            "inner": wl.inner, "prox_iters": prox, "lambda": lam, "power_iters": 20, "L": L,
+            "fista_iterations": rep["inner_total"], "restarts": rep["restarts"],
+            "residuals": rep["residuals"], "rel_err_vs_phantom": float((prec - p0).norm() / p0.norm()),
+            "rel_err_vs_ref": float((prec - p_ref).norm()) / nref,
+            "reference": {"inner": 300, "prox_iters": prox, "fista_iterations": rref["inner_total"],
+                          "seconds": t_ref},
+            "plain_seconds_to_2pct": t2, "ladder": ladder,
+            "warm_start": "plain cold-start solve; bench.py --warm trains the learned U-Net warm start and "
+                          "times warm against plain (the line's warm_start object)"}
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the platform string)."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return platform.processor() or platform.machine()
+
+
+def cpu_baseline(w):
+    """The FP64 oracle as it stands, on the host cores: the metric on a bounded sample of the workload
+    (all cores), plus the timings of the survey's CPU plan: one pair of the 32^3 workload on all
+    cores and on one, a 1-core sample of the workload, and a full oracle TV-Bregman solve of the
+    32^3 workload (5 x 20 FISTA iterations), all timed, not extrapolated, except where marked."""
+    import numpy as np
+
+    import oracle
+    from oracle import solver
+    from paper_1605_00133_gb300 import presets, synth
+    g = w.grid
+    Ts = 100
+    v, t, threads = oracle_pairs_per_s(w, Ts)
+    out = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+           "sample": (f"one oracle A + A^T on the full {g.nz}x{g.ny}x{g.nx} grid with T = {Ts} "
+                      f"({Ts - 1} time steps each way, {t:.1f} s), scaled to T = {g.T}"),
+           "cpu_model": cpu_model(), "nproc": os.cpu_count()}
+    Ts1 = 8
+    oracle.set_threads(1)
+    v1, t1, _ = oracle_pairs_per_s(w, Ts1)
+    out["one_core"] = {"value": v1, "unit": UNIT, "cores": 1,
+                       "sample": f"T = {Ts1} ({t1:.1f} s), scaled to T = {g.T} (extrapolated)"}
+    c1 = presets.workload("c1")
+    gc, sc = c1.grid, c1.sampling
+    p0 = c1.p0()
+    y = np.random.default_rng(0).standard_normal((gc.T, sc.m))
+    pair = {}
+    for n in (1, threads):
+        oracle.set_threads(n)
+        t0 = time.perf_counter()
+        oracle.forward(gc, sc, p0)
+        oracle.adjoint(gc, sc, y)
+        pair[n] = time.perf_counter() - t0
+    oracle.set_threads(threads)
+    out["c1_pair_seconds"] = {"one_core": pair[1], "all_cores": pair[threads],
+                              "workload": "c1: 32^3, T 64, rSP 256/1024"}
+    f = synth.add_relative_noise(oracle.forward(gc, sc, p0), 0.01, 4)
+    t0 = time.perf_counter()
+    L = solver.power_iteration(gc, sc, iters=20, seed=0)
+    _, info = solver.bregman(gc, sc, f, 1e-3, outer=c1.bregman_outer, inner=c1.inner, L=L, prox_iters=50)
+    ts = time.perf_counter() - t0
+    out["c1_solve"] = {"seconds": ts, "outer": c1.bregman_outer, "inner": c1.inner, "prox_iters": 50,
+                       "power_iters": 20, "fista_iterations": sum(i["iterations"] for i in info["inner"]),
+                       "cores": threads}
+    # the workload's reconstruction on the host: its pair count times the sampled pair time
+    out["solve_extrapolated_seconds"] = {"value": 300.0 / v, "note": "about 300 A + A^T pairs (5 x 50 FISTA "
+                                         "steps, restarts, 20 power iterations) x the all-core pair time"}
+    return out
 
 
 def warm_start_experiment(args, op, g, dev):

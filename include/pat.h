@@ -151,6 +151,17 @@ pat_status pat_sample_adjoint(pat_grid* grid, const float* f_dev, float* pbar_de
 pat_status pat_tv_prox(pat_grid* grid, const float* in_dev, float* out_dev, double alpha, int32_t iters,
                        int32_t bc, void* cuda_stream);
 
+/* BPppTV+ (Sec. 6.1; the method list's "BP followed by TV+ denoising"): the back-projection
+ * A^T C^T f of Eq. BP post-processed by positivity-constrained TV denoising, Eq. TV+Denoise with the
+ * back-projection in place of the time-reversal image:
+ *   p = argmin_{q >= 0} 1/2 ||q - A^T C^T f||^2 + alpha TV(q),
+ * with pat_tv_prox's TV (Neumann boundary) and solver (`iters` primal-dual iterations).  The
+ * back-projection is linear in f, so scaling f scales it.  f_dev: float[B][T][m] (read only);
+ * p_dev: float[B][Nz][Ny][Nx] (overwritten).  The first call on a grid allocates the prox
+ * workspace, like pat_tv_prox. */
+pat_status pat_bp_tv(pat_grid* grid, const float* f_dev, float* p_dev, double alpha, int32_t iters,
+                     void* cuda_stream);
+
 /* Parameters of pat_bregman_solve (App. B: eta = step_scale / L with step_scale 1.8, up to 5
  * backtracking halvings after a restart, stop when min E has not decreased 5 times in a row). */
 typedef struct {
@@ -200,11 +211,27 @@ pat_status pat_profile_read(pat_grid* grid, int32_t max_classes, char* names, do
 
 /* Device-side status of the grid's time-stepping kernels.  They stage their inputs with bulk
  * asynchronous copies and bound every wait for one (about a second); a wait that gives up is
- * recorded in a device word of the grid instead of hanging the GPU, and the results of the calls
- * since then are undefined.  Synchronises cuda_stream, then reads and clears the record: PAT_OK, or
- * PAT_ERR_TIMEOUT with pat_last_error() naming the copies that never landed.  pat_forward and
- * pat_adjoint do not synchronise, so they cannot report this themselves. */
+ * recorded in a device word of the grid instead of hanging the GPU, the CTA does not use the tile it
+ * waited for (and waits once more, bounded, before it exits), and the outputs of every call since
+ * the last check are invalid: repeat those calls.  Synchronises cuda_stream, then reads and clears
+ * the record: PAT_OK, or PAT_ERR_TIMEOUT with pat_last_error() naming the copies that never landed.
+ * pat_forward and pat_adjoint do not synchronise, so they cannot report this themselves;
+ * pat_bregman_solve checks it before returning. */
 pat_status pat_device_status(pat_grid* grid, void* cuda_stream);
+
+/* Test hook for the failure path above (the paper has no counterpart): while mask != 0, the line
+ * passes of later pat_forward / pat_adjoint calls on this grid leave out the bulk copies of the old
+ * state tiles that mask names (bit 1: state 1, bit 2: state 2; grids whose line tiles are 16 KB copy
+ * those tiles otherwise and are not affected) and give up waiting for them after `polls` polls
+ * (polls >= 1; each suspends for at most about a microsecond).  Nothing is then in flight, so the
+ * kernels return normally, their outputs are invalid, and pat_device_status reports
+ * PAT_ERR_TIMEOUT.  mask = 0 restores normal operation and the default poll limit. */
+pat_status pat_debug_copy_fault(pat_grid* grid, int32_t mask, int32_t polls);
+
+/* Process-wide cap on the device workspace of one grid, in bytes (0, the default: no cap).
+ * pat_create_grid computes a grid's workspace on the host and returns PAT_ERR_OOM, before touching
+ * the device, when it exceeds the cap: for callers that share the GPU under a memory budget. */
+pat_status pat_set_workspace_limit(int64_t bytes);
 
 /* Message for the last failed call on this thread ("" if none). Valid until the next call. */
 const char* pat_last_error(void);

@@ -18,7 +18,8 @@ STATUS_NAMES = {0: "PAT_OK", 1: "PAT_ERR_INVALID_ARG", 2: "PAT_ERR_CUDA", 3: "PA
 EXPORTS = ["pat_create_grid", "pat_destroy_grid", "pat_grid_info", "pat_workspace_bytes",
            "pat_forward", "pat_adjoint", "pat_sample", "pat_sample_adjoint", "pat_profile_enable",
            "pat_profile_read", "pat_last_error", "pat_version", "pat_forward_noalloc", "pat_tv_prox",
-           "pat_bregman_solve", "pat_get_indices", "pat_device_status"]
+           "pat_bregman_solve", "pat_get_indices", "pat_device_status", "pat_debug_copy_fault",
+           "pat_set_workspace_limit", "pat_bp_tv"]
 # include/pat_unet.h (learned warm start)
 UNET_EXPORTS = ["pat_unet_conv3", "pat_unet_wgrad_scratch", "pat_unet_conv3_wgrad", "pat_unet_cast_weights",
                 "pat_unet_relu_bwd", "pat_unet_pool", "pat_unet_pool_bwd_add", "pat_unet_up", "pat_unet_up_bwd",
@@ -96,11 +97,17 @@ def load() -> ctypes.CDLL:
         L.pat_get_indices.restype = ctypes.c_int
         L.pat_tv_prox.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_int32, ctypes.c_int32, vp]
         L.pat_tv_prox.restype = ctypes.c_int
+        L.pat_bp_tv.argtypes = [vp, vp, vp, ctypes.c_double, ctypes.c_int32, vp]
+        L.pat_bp_tv.restype = ctypes.c_int
         L.pat_bregman_solve.argtypes = [vp, vp, vp, vp, ctypes.POINTER(SolveParams),
                                         ctypes.POINTER(SolveReport), vp]
         L.pat_bregman_solve.restype = ctypes.c_int
         L.pat_device_status.argtypes = [vp, vp]
         L.pat_device_status.restype = ctypes.c_int
+        L.pat_debug_copy_fault.argtypes = [vp, ctypes.c_int32, ctypes.c_int32]
+        L.pat_debug_copy_fault.restype = ctypes.c_int
+        L.pat_set_workspace_limit.argtypes = [ctypes.c_int64]
+        L.pat_set_workspace_limit.restype = ctypes.c_int
         L.pat_profile_enable.argtypes = [vp, ctypes.c_int32]
         L.pat_profile_enable.restype = ctypes.c_int
         L.pat_profile_read.argtypes = [vp, ctypes.c_int32, ctypes.c_char_p, ctypes.POINTER(ctypes.c_double),

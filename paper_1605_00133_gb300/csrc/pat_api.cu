@@ -13,6 +13,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <complex>
 #include <mutex>
 #include <string>
@@ -24,6 +25,10 @@
 using namespace pat;
 
 namespace {
+
+// poll limit of the line passes' bounded waits for their bulk copies (each poll suspends for at
+// most about a microsecond: about a second in all)
+constexpr int kDefaultPolls = 1 << 20;
 
 thread_local std::string g_err;
 
@@ -38,6 +43,9 @@ pat_status cuda_fail(cudaError_t e, const char* where) {
 }
 
 bool pow2_in(int v, int lo, int hi) { return v >= lo && v <= hi && (v & (v - 1)) == 0; }
+
+// process-wide cap on the device workspace one grid may hold (pat_set_workspace_limit); 0 = none
+std::atomic<int64_t> g_ws_limit{0};
 
 }  // namespace
 
@@ -335,19 +343,12 @@ pat_status pat_create_grid(const pat_grid_desc* desc, const pat_sampling_desc* s
     pat_status st = validate(desc, sampling);
     if (st != PAT_OK) return st;
 
-    int dev = -1;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-    cudaDeviceProp prop;
-    e = cudaGetDeviceProperties(&prop, dev);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceProperties");
-    if (prop.major * 10 + prop.minor != 103)
-        return fail(PAT_ERR_UNSUPPORTED, std::string("libpat is built for sm_103a only; device is ") + prop.name);
-
     pat_grid* G = new pat_grid();
     G->d = *desc;
-    G->device = dev;
+    G->device = -1;
     G->kind = sampling->kind;
+    G->t.polls = kDefaultPolls;
+    G->t.skip = 0;
     G->bytes = 0;
     if (G->d.sensor_z < 0) G->d.sensor_z = G->d.pml_size;
     if (!(G->d.dt > 0)) G->d.dt = G->d.cfl * G->d.dx / G->d.c;
@@ -383,9 +384,34 @@ pat_status pat_create_grid(const pat_grid_desc* desc, const pat_sampling_desc* s
     g.T = G->d.T;
     g.m_plane = M;
 
+    // the workspace cap is checked on the host, before the device is touched
+    const WsLayout layout = workspace_layout(g, G->kind);
+    const int64_t limit = g_ws_limit.load();
+    if (limit > 0 && (int64_t)layout.total > limit) {
+        delete G;
+        return fail(PAT_ERR_OOM, "pat_create_grid: the workspace needs " + std::to_string(layout.total) +
+                                     " bytes, above the limit of " + std::to_string(limit) +
+                                     " bytes set by pat_set_workspace_limit");
+    }
+
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        delete G;
+        return cuda_fail(e, "cudaGetDevice");
+    }
+    cudaDeviceProp prop;
+    e = cudaGetDeviceProperties(&prop, dev);
+    if (e != cudaSuccess || prop.major * 10 + prop.minor != 103) {
+        delete G;
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceProperties");
+        return fail(PAT_ERR_UNSUPPORTED, std::string("libpat is built for sm_103a only; device is ") + prop.name);
+    }
+    G->device = dev;
+
     // workspace: one allocation, carved as workspace_carve describes
     {
-        const WsLayout L = workspace_layout(g, G->kind);
+        const WsLayout& L = layout;
         unsigned char* base = nullptr;
         st = dalloc(G, (void**)&base, L.total, "workspace");
         if (st == PAT_OK) workspace_carve(g, L, base, &G->w);
@@ -519,6 +545,22 @@ pat_status pat_device_status(pat_grid* G, void* stream) {
     if (word & 2) what += " state-1 tile";
     if (word & 4) what += " state-2 tile";
     return fail(PAT_ERR_TIMEOUT, "pat_device_status: a line pass gave up waiting for its bulk copy of the" + what);
+}
+
+pat_status pat_debug_copy_fault(pat_grid* G, int32_t mask, int32_t polls) {
+    g_err.clear();
+    if (!G) return fail(PAT_ERR_INVALID_ARG, "pat_debug_copy_fault: NULL grid");
+    if ((mask & ~6) != 0 || polls < 0) return fail(PAT_ERR_INVALID_ARG, "pat_debug_copy_fault: mask bits 1, 2 only; polls >= 0");
+    G->t.skip = mask;
+    G->t.polls = (mask == 0 || polls == 0) ? kDefaultPolls : polls;
+    return PAT_OK;
+}
+
+pat_status pat_set_workspace_limit(int64_t bytes) {
+    g_err.clear();
+    if (bytes < 0) return fail(PAT_ERR_INVALID_ARG, "pat_set_workspace_limit: bytes must be >= 0");
+    g_ws_limit.store(bytes);
+    return PAT_OK;
 }
 
 pat_status pat_profile_enable(pat_grid* G, int32_t enable) {

@@ -200,6 +200,8 @@ static LineArgs line_base(const Geom& g, const DeviceTables& t, const Workspace&
     a.ncols = g.ncols[ax];
     a.tw = t.tw[ax];
     a.err = t.err;
+    a.polls = t.polls;
+    a.skip = t.skip;
     a.twi = t.twi[ax];
     a.twf = t.twf[ax];
     a.st1 = w.ms[ax][0];

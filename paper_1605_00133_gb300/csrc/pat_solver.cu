@@ -473,6 +473,28 @@ extern "C" pat_status pat_tv_prox(pat_grid* G, const float* in, float* out, doub
     return tv_prox_run(c, p, out, alpha, iters, 1);
 }
 
+extern "C" pat_status pat_bp_tv(pat_grid* G, const float* f, float* p_out, double alpha, int32_t iters,
+                                void* stream) {
+    set_error(PAT_OK, "");
+    if (!G) return set_error(PAT_ERR_INVALID_ARG, "pat_bp_tv: NULL grid");
+    if (!p_out || (!f && G->m > 0)) return set_error(PAT_ERR_INVALID_ARG, "pat_bp_tv: NULL buffer");
+    if (!(alpha >= 0) || iters < 0) return set_error(PAT_ERR_INVALID_ARG, "pat_bp_tv: need alpha >= 0, iters >= 0");
+    pat_status st = check_grid_device(G);
+    if (st != PAT_OK) return st;
+    if ((st = ensure_ws(G, false)) != PAT_OK) return st;
+    Ctx c;
+    c.G = G;
+    c.st = (cudaStream_t)stream;
+    c.N = (size_t)G->g.B * G->g.nreal;
+    c.D = 0;
+    c.td = TvDims{G->g.nz, G->g.ny, G->g.nx, (size_t)G->g.nreal, c.N};
+    // back-projection A^T C^T f (Eq. BP) into the prox's input buffer, then its TV+ denoising
+    float* bp = G->sw.z;
+    cudaError_t e = run_adjoint(G->g, G->t, G->w, G->s, G->kind, G->m, f, bp, c.st, nullptr);
+    if (e != cudaSuccess) return set_cuda_error(e, "pat_bp_tv adjoint");
+    return tv_prox_run(c, bp, p_out, alpha, iters, 1);
+}
+
 extern "C" pat_status pat_bregman_solve(pat_grid* G, const float* f, const float* warm, float* p_out,
                                         const pat_solve_params* params, pat_solve_report* report, void* stream) {
     set_error(PAT_OK, "");
@@ -528,5 +550,7 @@ extern "C" pat_status pat_bregman_solve(pat_grid* G, const float* f, const float
     }
     PAT_CUDA(cudaMemcpyAsync(p_out, w.xp, c.N * sizeof(float), cudaMemcpyDeviceToDevice, c.st), "solution copy");
     if (report) *report = rep;
-    return PAT_OK;
+    // a time-step kernel whose bounded wait for a bulk copy gave up makes every result since then
+    // undefined; the solve has synchronised anyway, so it reads (and clears) the record itself
+    return pat_device_status(G, stream);
 }

@@ -137,6 +137,16 @@ class PatOperator:
                                            0, _stream_ptr(p.device)))
         return out
 
+    def bp_tv(self, f: torch.Tensor, alpha: float, iters: int = 200, out: torch.Tensor = None):
+        """BPppTV+: argmin_{q >= 0} 1/2 ||q - A^T C^T f||^2 + alpha TV(q) (pat_bp_tv)."""
+        self._check_tensor(f, self.data_shape, "f")
+        if out is None:
+            out = torch.empty(self.image_shape, device=f.device, dtype=torch.float32)
+        self._check_tensor(out, self.image_shape, "out")
+        _lib.check(_lib.load().pat_bp_tv(self._h, f.data_ptr(), out.data_ptr(), float(alpha), int(iters),
+                                         _stream_ptr(f.device)))
+        return out
+
     def bregman_solve(self, f: torch.Tensor, lam: float, outer: int = 5, inner: int = 50,
                       prox_iters: int = 100, L: float = 0.0, power_iters: int = 20, seed: int = 0,
                       step_scale: float = 1.8, max_backtrack: int = 5, stall: int = 5,

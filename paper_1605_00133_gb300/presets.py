@@ -104,6 +104,7 @@ def workload(name: str, seed: int = 0) -> Workload:
     c2  64x128x128, dx 100 um, T 400, 10-pt PML, 20 branching tubes, rSP 12.5 % (2048/16384).
     c3  c2 grid with scrambled-Hadamard 0/1 patterns, m = 2048 of 16384.
     c4  128x256x256, dx 50 um, T 800, 10-pt PML, 60 tubes, rSP 1/16 (4096/65536).
+    c2gsp  c2 with regular-grid single points, gSP-16 (every 4th point in y and x: 1024/16384).
     """
     if name == "c1":
         g = Grid(32, 32, 32, dx=100e-6, T=64, pml_size=8)
@@ -121,6 +122,10 @@ def workload(name: str, seed: int = 0) -> Workload:
         g = Grid(128, 256, 256, dx=50e-6, T=800, pml_size=10)
         return Workload(name, g, make_sampling(g, KIND_RSP, 4096, seed), "tubes60", seed,
                         bregman_outer=5, inner=50)
+    if name == "c2gsp":
+        g = Grid(64, 128, 128, dx=100e-6, T=400, pml_size=10)
+        s = Sampling(KIND_RSP, 1024, indices=synth.gsp_indices(g.ny, g.nx, 4))
+        return Workload(name, g, s, "tubes20", seed, bregman_outer=5, inner=50)
     raise ValueError(f"unknown workload {name!r}")
 
 

@@ -19,18 +19,14 @@ def dev():
     return torch.device("cuda", 0)
 
 
-@pytest.mark.parametrize("kind", [presets.KIND_RSP, presets.KIND_SHD01])
-def test_gradient_of_data_misfit(dev, oracle_mod, kind):
+def _check_misfit_gradient(dev, oracle_mod, g, s, p0):
     """L(p0) = 1/2 ||C A p0 - f||^2: autograd gives A^T C^T (C A p0 - f); compared with the FP64
     oracle's adjoint of the FP64 residual, and with a central difference along a random direction
     (exact for a quadratic: (L(p+ev) - L(p-ev)) / 2e = <grad L(p), v>)."""
     from paper_1605_00133_gb300.autograd import pat_forward
     from paper_1605_00133_gb300.operators import PatOperator
-    g = presets.Grid(16, 32, 32, T=20, pml_size=4)
-    s = presets.make_sampling(g, kind, 128, 2)
     op = PatOperator(g, s)
     rng = np.random.default_rng(3)
-    p0 = synth.gaussian_balls(g.shape, 2, 2.0, 5, pml=4)
     f = oracle_mod.forward(g, s, p0)
     f = f + 0.05 * np.abs(f).max() * rng.standard_normal((g.T, s.m))
     x = torch.tensor(p0, dtype=torch.float32, device=dev).reshape(op.image_shape).requires_grad_(True)
@@ -55,6 +51,21 @@ def test_gradient_of_data_misfit(dev, oracle_mod, kind):
     fd = (L(p0 + eps * v) - L(p0 - eps * v)) / (2 * eps)
     # central differences are exact for a quadratic; what remains is FP32 rounding of C A p
     assert fd == pytest.approx(float(np.sum(grad * v)), rel=1e-3)
+    op.close()
+
+
+@pytest.mark.parametrize("kind", [presets.KIND_RSP, presets.KIND_SHD01])
+def test_gradient_of_data_misfit(dev, oracle_mod, kind):
+    g = presets.Grid(16, 32, 32, T=20, pml_size=4)
+    s = presets.make_sampling(g, kind, 128, 2)
+    _check_misfit_gradient(dev, oracle_mod, g, s, synth.gaussian_balls(g.shape, 2, 2.0, 5, pml=4))
+
+
+def test_gradient_on_the_patterned_interrogation_workload(dev, oracle_mod):
+    """The patterned-interrogation workload's grid, phantom and patterns (64x128x128, m = 2048 of
+    the 16384 scrambled Hadamard 0/1 patterns of the 128x128 plane), T = 16."""
+    w = presets.shrink(presets.workload("c3"), 16)
+    _check_misfit_gradient(dev, oracle_mod, w.grid, w.sampling, w.p0())
 
 
 def test_adjoint_function_backward_is_forward(dev, oracle_mod):

@@ -1,9 +1,15 @@
 """GPU parity: libpat (FP32, CUDA) against the FP64 oracle, through the C ABI.
 
-Tolerance: relative L2 error <= 1e-5 for A and A^T in FP32.  The scheme needs ten 3D FFTs per time
-step; an FP32 restatement of the same recurrence with a library FFT lands at ~1.3e-6 after 100
-steps and grows like sqrt(T), so 1e-5 leaves headroom up to T = 400.  Index work (rSP gather and
-scatter, scrambled-Hadamard sampling of integer-valued planes) must match bit for bit.
+Tolerance: relative L2 error <= 1e-5 for A, and for A^T on data in the range of A, in FP32.  Each
+time step takes twelve line transforms in FP32, whose rounding accumulates over the steps like a
+random walk; smooth data at T = 400 end near 3e-6.  The adjoint of broadband data (white noise, or
+the residual of a solver iterate, whose noise part is white) injects every time step's rounding at
+every frequency, and there an FP32 evaluation of the recurrence cannot reach 1e-5 at T = 400: the
+independent FP32 restatement in fp32_floor.py (library FFTs, float32) lands at 2e-5 on white noise,
+and its error comes from the transforms alone (float32 state updates with float64 transforms give
+3e-7).  Those cases are held to 1.5 times that restatement's error on the same data, computed in the
+test.  Index work (rSP gather and scatter, scrambled-Hadamard sampling of integer-valued planes)
+must match bit for bit.
 """
 import numpy as np
 import pytest
@@ -193,12 +199,14 @@ def test_device_index_sets_are_bit_exact(dev, name):
     op.close()
 
 
+@pytest.mark.parametrize("plane,m", [(64, 700), (128, 2048)])
 @pytest.mark.parametrize("kind", [presets.KIND_RSP, presets.KIND_SHD01, presets.KIND_SHDPM])
-def test_sampling_is_bit_exact_on_integer_planes(oracle_mod, dev, kind):
+def test_sampling_is_bit_exact_on_integer_planes(oracle_mod, dev, kind, plane, m):
     """Integer-valued planes: every sum in C and C^T is exact in FP32 and FP64 alike (M = 4^k makes
-    1/sqrt(M) a power of two)."""
-    g = presets.Grid(8, 64, 64, T=5, pml_size=2)
-    s = presets.make_sampling(g, kind, 700, 9)
+    1/sqrt(M) a power of two).  The 128x128 plane is the patterned-interrogation workload's
+    (M = 16384, m = 2048): its 64 KB FWHT plane takes the shared-memory opt-in beyond 48 KB."""
+    g = presets.Grid(8, plane, plane, T=5, pml_size=2)
+    s = presets.make_sampling(g, kind, m, 9)
     op = make_op(g, s)
     rng = np.random.default_rng(13)
     pbar = rng.integers(-40, 40, size=(g.T, g.m_plane)).astype(np.float64)
@@ -212,6 +220,24 @@ def test_sampling_is_bit_exact_on_integer_planes(oracle_mod, dev, kind):
 
 
 # ------------------------------------------------------------------------------ full workload sizes
+
+@pytest.mark.parametrize("kind", [presets.KIND_SHD01, presets.KIND_SHDPM])
+def test_c3_hadamard_workload_matches_oracle_reduced_T(oracle_mod, dev, kind):
+    """The patterned-interrogation workload at full size (Sec. 3.1.2, Sec. 4.3): 64x128x128 grid,
+    vessel phantom, m = 2048 of the 16384 scrambled Hadamard patterns of the 128x128 plane (0/1 as a
+    DMD shows them, and the orthonormal +-1/sqrt(M) form), T = 16: forward and adjoint against the
+    FP64 oracle."""
+    w = presets.shrink(presets.workload("c3"), 16)
+    g = w.grid
+    s = w.sampling if kind == presets.KIND_SHD01 else presets.make_sampling(g, kind, 2048, w.seed)
+    assert g.m_plane == 16384 and s.m == 2048
+    p0 = w.p0()
+    op = make_op(g, s)
+    assert rel(gpu_forward(op, p0, dev), oracle_mod.forward(g, s, p0)) < TOL
+    y = np.random.default_rng(17).standard_normal((g.T, s.m))
+    assert rel(gpu_adjoint(op, y, dev), oracle_mod.adjoint(g, s, y)) < TOL
+    op.close()
+
 
 def test_c2_dot_product_fp32(dev):
     """<C A x, y> = <x, A^T C^T y> on the full 64x128x128, T = 400 workload, GPU FP32 (inner products
@@ -259,10 +285,10 @@ def test_c2_forward_matches_oracle_reduced_T(oracle_mod, dev):
 def test_c2_forward_and_adjoint_match_oracle_full_T(oracle_mod, dev):
     """The headline workload end to end: 64x128x128, T = 400, rSP 12.5 %, vessel phantom.
     Forward (measured 3.2e-6) and the adjoint of realistic data, C A p0 + 1 % noise (measured
-    3.3e-6), within 1e-5.  The adjoint of white-noise data carries broadband content injected at
-    every step; its FP32 floor grows faster with T (an independent FP32 restatement of the same
-    recurrence with an accurate library FFT gives the same error: 7.2e-6 at T = 100), measured
-    2.3e-5 at T = 400, so that case is held to 4e-5."""
+    3.3e-6), within 1e-5.  Two broadband adjoint inputs, white noise and the data residual
+    C A p - f of the under-converged iterate p = 0.9 p0 (the solver's A^T input), are held to 1.5
+    times the error of the FP32 restatement of the same recurrence on the same data."""
+    import fp32_floor as ff
     w = presets.workload("c2")
     g, s = w.grid, w.sampling
     p0 = w.p0()
@@ -271,8 +297,14 @@ def test_c2_forward_and_adjoint_match_oracle_full_T(oracle_mod, dev):
     assert rel(gpu_forward(op, p0, dev), f_ref) < TOL
     y = synth.add_relative_noise(f_ref, 0.01, 4)
     assert rel(gpu_adjoint(op, y, dev), oracle_mod.adjoint(g, s, y)) < TOL
-    yw = np.random.default_rng(0).standard_normal((g.T, s.m))
-    assert rel(gpu_adjoint(op, yw, dev), oracle_mod.adjoint(g, s, yw)) < 4e-5
+    scheme = ff.Scheme(g, np.float32)
+    cases = {"white": np.random.default_rng(0).standard_normal((g.T, s.m)), "residual": 0.9 * f_ref - y}
+    for name, yb in cases.items():
+        ref = oracle_mod.adjoint(g, s, yb)
+        floor = rel(scheme.adjoint_plane(oracle_mod.sample_T(s, yb, g.m_plane)), ref)
+        err = rel(gpu_adjoint(op, yb, dev), ref)
+        assert err < 1.5 * floor, (name, err, floor)
+    op.close()
 
 
 # ------------------------------------------------------------------------------ large grid (c4)

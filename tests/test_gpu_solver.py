@@ -92,6 +92,28 @@ def test_bregman_solve_matches_oracle(dev, sol, c1_problem):
     np.testing.assert_allclose(rep["residuals"], info["residuals"], rtol=1e-4)
 
 
+@pytest.mark.slow
+def test_bregman_solve_on_the_c2_grid_matches_oracle(dev, sol, oracle_mod):
+    """The headline grid and sampling (64x128x128, 10-voxel PML, rSP 2048 of 16384, vessel phantom)
+    at T = 16: 2 Bregman steps x 4 FISTA iterations, 20 prox iterations, L from 5 oracle power
+    iterations; iterate for iterate against the FP64 oracle like the 32^3 case."""
+    w = presets.shrink(presets.workload("c2"), 16)
+    g, s = w.grid, w.sampling
+    f = synth.add_relative_noise(oracle_mod.forward(g, s, w.p0()), 0.01, 4)
+    L = sol.power_iteration(g, s, iters=5, seed=0)
+    lam = 2e-4
+    p_ref, info = sol.bregman(g, s, f, lam, outer=2, inner=4, L=L, prox_iters=20)
+    op = op_for(g, s)
+    ft = torch.tensor(f, dtype=torch.float32, device=dev).reshape(op.data_shape)
+    p, rep = op.bregman_solve(ft, lam, outer=2, inner=4, prox_iters=20, L=L)
+    got = p.double().cpu().numpy().reshape(g.shape)
+    assert rep["restarts"] == sum(i["restarts"] for i in info["inner"])
+    assert rep["inner_total"] == sum(i["iterations"] for i in info["inner"])
+    assert rel(got, p_ref) < 1e-4
+    np.testing.assert_allclose(rep["residuals"], info["residuals"], rtol=1e-4)
+    op.close()
+
+
 def test_power_iteration_on_gpu_matches_oracle_estimate(dev, sol, c1_problem):
     """The library starts the power iteration from SplitMix64/Box-Muller normals of the given seed
     (the same stream synth.Stream produces), rounded to FP32; the oracle runs from that start."""

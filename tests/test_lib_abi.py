@@ -104,3 +104,25 @@ def test_no_gpu_means_an_error_not_a_fallback(lib):
     with pytest.raises(RuntimeError):
         from paper_1605_00133_gb300 import PatOperator, presets
         PatOperator(presets.Grid(16, 16, 16, T=4, pml_size=2), presets.Sampling(0, 256))
+
+
+def test_workspace_cap_returns_oom_before_any_device_call(lib):
+    """pat_set_workspace_limit: a grid whose workspace exceeds the cap is refused with PAT_ERR_OOM
+    from the host-side size computation alone, whether or not a GPU is present."""
+    from paper_1605_00133_gb300 import _lib
+    d = _desc(nz=64, ny=128, nx=128, T=400, pml_size=10)
+    s = _lib.SamplingDesc(0, 0, None, None, None)
+    h = ctypes.c_void_p()
+    try:
+        assert lib.pat_set_workspace_limit(-1) == 1
+        assert lib.pat_set_workspace_limit(10 << 20) == 0
+        assert lib.pat_create_grid(ctypes.byref(d), ctypes.byref(s), ctypes.byref(h)) == 3
+        assert not h.value
+        assert b"pat_set_workspace_limit" in lib.pat_last_error()
+    finally:
+        assert lib.pat_set_workspace_limit(0) == 0
+
+
+def test_fault_hook_checks_its_arguments(lib):
+    assert lib.pat_debug_copy_fault(None, 2, 4) == 1
+    assert lib.pat_device_status(None, None) == 1

@@ -1,7 +1,7 @@
 """pat_forward_noalloc: the forward operator for callers that cannot allocate device memory at call
 time (reconstruction loops that reserve their whole device budget at start-up).  Its scratch is a
-static 64 MiB device array inside libpat, so its results must equal pat_forward's, call after call,
-and grids that do not fit must be refused with a clear message.
+static 64 MiB device array inside libpat, so its results must equal pat_forward's and the FP64
+oracle's, call after call, and grids that do not fit must be refused with a clear message.
 
 This file is named to be collected last, so a failure here leaves every other test already run.
 """
@@ -56,6 +56,27 @@ def test_noalloc_forward_matches_pat_forward_twice(dev, kind):
         a, b = got.double().cpu().numpy(), ref.double().cpu().numpy()
         assert np.isfinite(a).all()
         assert np.linalg.norm(a - b) / np.linalg.norm(b) <= TOL, call
+    op.close()
+
+
+def test_noalloc_forward_matches_the_oracle(oracle_mod, dev):
+    """Against the FP64 oracle directly (not only against pat_forward, which shares its kernels):
+    the c1 workload, two calls in a row with different phantoms."""
+    from paper_1605_00133_gb300 import _lib
+    from paper_1605_00133_gb300.operators import PatOperator
+    lib = _lib.load()
+    w = presets.workload("c1")
+    g, s = w.grid, w.sampling
+    op = PatOperator(g, s)
+    for call in range(2):
+        p0 = w.p0(seed_offset=call)
+        x = torch.tensor(p0, dtype=torch.float32, device=dev).reshape(op.image_shape)
+        got = torch.full(op.data_shape, float("nan"), device=dev)
+        _call(lib, "pat_forward_noalloc", op, x, got)
+        torch.cuda.synchronize()
+        ref = oracle_mod.forward(g, s, p0)
+        a = got.double().cpu().numpy().reshape(ref.shape)
+        assert np.linalg.norm(a - ref) / np.linalg.norm(ref) <= TOL, call
     op.close()
 
 

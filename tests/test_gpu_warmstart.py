@@ -1,6 +1,7 @@
-"""Learned warm start pipeline on a small grid: training pairs from the operators and the plain
-solver, training that lowers the loss, and the warm-vs-plain evaluation, whose plain arm at the
-full schedule reproduces its own reference exactly (the solver is deterministic)."""
+"""Learned warm start on a small grid: training pairs from the operators and the plain solver,
+training that lowers the loss, and what the trained network gains.  On held-out phantoms, a solve
+started from the network's output is closer to the converged plain reconstruction than the plain
+cold-start solve after the same number of FISTA iterations, and reaches 10 % of it sooner."""
 import pytest
 
 torch = pytest.importorskip("torch")
@@ -17,7 +18,7 @@ def dev():
     return torch.device("cuda", 0)
 
 
-def test_pipeline_trains_and_evaluates(dev):
+def test_trained_warm_start_beats_the_cold_start(dev):
     from paper_1605_00133_gb300 import presets, unet, warmstart
     from paper_1605_00133_gb300.operators import PatOperator
     g = presets.Grid(16, 32, 32, T=24, pml_size=4)
@@ -28,17 +29,21 @@ def test_pipeline_trains_and_evaluates(dev):
     _, rep = op.bregman_solve(torch.zeros(op.data_shape, device=dev), lam, outer=1, inner=1, prox_iters=1,
                               power_iters=10)
     L = rep["L"]
-    pairs = warmstart.make_pairs(op, wl, 4, 100, lam, wl.bregman_outer, wl.inner, L, prox_iters=20)
-    test = warmstart.make_pairs(op, wl, 1, 900, lam, wl.bregman_outer, wl.inner, L, prox_iters=20)
+    pairs = warmstart.make_pairs(op, wl, 24, 100, lam, wl.bregman_outer, 60, L, prox_iters=20)
+    test = warmstart.make_pairs(op, wl, 2, 900, lam, wl.bregman_outer, 60, L, prox_iters=20)
     net = unet.WarmStartUNet(g.nz, g.ny, g.nx, seed=0)
     net.s_in = warmstart.input_scale(pairs)
-    hist = warmstart.train(net, pairs, 8, lr=1e-3, seed=0)
-    assert hist[-1] < hist[0], hist
-    ev = warmstart.evaluate(op, net, test, lam, wl.bregman_outer, [5, wl.inner], L, prox_iters=20)
-    assert len(ev) == 1
-    e = ev[0]
-    assert e["plain"][-1]["rel_err"] <= 1e-6  # same schedule, same start, same L: the reference itself
-    assert e["plain_seconds_to_tol"] is not None
-    assert e["warm"][0]["inner"] == 0 and e["warm"][0]["rel_err"] == e["network_rel_err"]
-    assert all(t["seconds"] > 0 for t in e["plain"] + e["warm"])
+    hist = warmstart.train(net, pairs, 16, lr=1e-3, seed=0)
+    assert hist[-1] < 0.5 * hist[0], hist
+    # the second tolerance is out of reach, so both arms run the whole schedule
+    ev = warmstart.evaluate(op, net, test, lam, wl.bregman_outer, [5, 10, 20, 40], L, inner_ref=300,
+                            tols=(0.10, 1e-4), prox_iters=20)
+    for e in ev:
+        plain = {t["inner"]: t["rel_err"] for t in e["plain"]}
+        warm = {t["inner"]: t["rel_err"] for t in e["warm"]}
+        assert warm[0] == e["network_rel_err"] and e["network_rel_err"] < 1.0
+        for n in (5, 10):
+            assert warm[n] < plain[n], (n, warm, plain)
+        t = e["seconds_to"]["0.1"]
+        assert t["warm"] is not None and (t["plain"] is None or t["warm"] < t["plain"]), t
     op.close()

@@ -557,7 +557,7 @@ def warm_start_experiment(args, op, g, dev):
 
 
 # sources that do not take part in A or A^T (solver, learned warm start): excluded from the hash
-_NOT_OPERATOR = ("pat_solver.cu", "pat_unet.cu")
+_NOT_OPERATOR = ("pat_solver.cu", "pat_unet.cu", "pat_unet_tc.cu")
 
 
 _C_TOKENS = re.compile(r'"(?:\\.|[^"\\])*"|//[^\n]*|/\*.*?\*/', re.S)

@@ -11,9 +11,11 @@
  *   of a wider buffer is passed as base + offset with the buffer's ld).  Channel counts and strides
  *   are multiples of 16 and pointers 16-byte aligned.  Convolutions are 3x3x3, stride 1, zero
  *   padding 1, no bias; weights are [27][Cout][Cin] (tap t = 9 (dz+1) + 3 (dy+1) + (dx+1)).
- *   Tensor cores: mma.sync m16n8k16 BF16 with FP32 accumulation.  All calls are ordered on the
- *   given stream and return without synchronising; invalid arguments return PAT_ERR_INVALID_ARG
- *   before anything is launched.
+ *   Tensor cores: BF16 operands with FP32 accumulation; the convolution (and with transposed
+ *   weights its data gradient) on tcgen05 with tensor-memory accumulators and TMA-staged operands,
+ *   the weight gradient on mma.sync m16n8k16.  All calls are ordered on the given stream and return
+ *   without synchronising; invalid arguments return PAT_ERR_INVALID_ARG before anything is
+ *   launched.
  */
 #ifndef PAT_UNET_H
 #define PAT_UNET_H
@@ -28,9 +30,15 @@ extern "C" {
 
 /* y = act(conv3(x, w)): x [V][ldx] (cin channels), w bf16 [27][cout][cin], y [V][ldy] (cout
  * channels, overwritten).  relu != 0 applies max(0, .).  cin in 16..512 and cout in 16..1024,
- * multiples of 16. */
+ * multiples of 16.  The kernel bounds its waits; one that gives up is reported by
+ * pat_unet_device_status. */
 pat_status pat_unet_conv3(const void* x, int32_t ldx, int32_t cin, const void* w, int32_t cout, void* y,
                           int32_t ldy, int32_t D, int32_t H, int32_t W, int32_t relu, void* cuda_stream);
+
+/* Synchronises cuda_stream, then reads and clears the device word in which the tensor-core
+ * convolutions record a bounded wait that gave up: PAT_OK, or PAT_ERR_TIMEOUT (the outputs of the
+ * convolutions since the last check are invalid). */
+pat_status pat_unet_device_status(void* cuda_stream);
 
 /* Weight gradient of pat_unet_conv3: dw[t][co][ci] = sum_v dy[v][co] x[v + off_t][ci] (FP32,
  * overwritten), dy the gradient at the convolution's output (after the activation's backward);

@@ -9,7 +9,8 @@ from concurrent.futures import ThreadPoolExecutor
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libpat.so")
-SOURCES = ["pat_api.cu", "pat_run.cu", "pat_zpass.cu", "pat_sample.cu", "pat_solver.cu", "pat_unet.cu"] + [
+SOURCES = ["pat_api.cu", "pat_run.cu", "pat_zpass.cu", "pat_sample.cu", "pat_solver.cu", "pat_unet.cu",
+           "pat_unet_tc.cu"] + [
     f"pat_plane_nx{n}.cu" for n in (8, 16, 32, 64, 128, 256)] + [
     f"pat_line_l{n}.cu" for n in (8, 16, 32, 64, 128, 256)]
 HEADERS = ["pat_fft.cuh", "pat_internal.h", "pat_kargs.h", "pat_plane.cuh", "pat_line.cuh",

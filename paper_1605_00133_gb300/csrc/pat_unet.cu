@@ -1,12 +1,7 @@
 // pat_unet.cu - layers of the learned warm start (a 3D U-Net mapping A^T C^T f to a starting image
-// for the TV-Bregman solver): 3x3x3 convolutions on the tensor cores (BF16 operands, FP32
-// accumulation, mma.sync m16n8k16), their weight gradients, and the elementwise layers around them.
-//
-// Convolution as an implicit GEMM: M = voxels, N = output channels, K = 27 taps x input channels.
-// A CTA owns 128 consecutive voxels (8 warps x 16 rows) and BN output channels; each K step is one
-// tap and 16 input channels, staged in shared memory by cp.async (zero-filled where the tap falls
-// outside the volume) in a two-stage pipeline.  Shared rows are 24 BF16 (48 bytes): 16-byte aligned
-// for the copies and conflict-free for the fragment loads.
+// for the TV-Bregman solver): the C ABI of the 3x3x3 convolutions (forward and data gradient on the
+// tcgen05 tensor cores, pat_unet_tc.cu), their weight gradients (BF16 operands, FP32 accumulation,
+// mma.sync m16n8k16), and the elementwise layers around them.
 //
 // Weight gradient: per tap t a GEMM with M = output channels, N = input channels and K = voxels,
 // split over voxel chunks (grid.x) and taps (grid.y), both operands staged transposed in shared
@@ -21,12 +16,16 @@
 #include "../../include/pat_unet.h"
 #include "pat_internal.h"
 
+namespace pat {
+cudaError_t conv3_tc(const void* x, int ldx, int cin, const void* w, int cout, void* y, int ldy, int D, int H,
+                     int W, int relu, cudaStream_t st);
+cudaError_t unet_take_status(int* word, cudaStream_t st);
+}  // namespace pat
+
 namespace {
 
 typedef __nv_bfloat16 bf16;
 
-constexpr int kBM = 128;     // voxels per convolution CTA
-constexpr int kPitch = 24;   // shared row pitch (BF16)
 constexpr int kChunk = 2048; // voxels per weight-gradient CTA
 
 __device__ __forceinline__ void mma16816(float* d, const uint32_t* a, const uint32_t* b) {
@@ -36,97 +35,7 @@ __device__ __forceinline__ void mma16816(float* d, const uint32_t* a, const uint
         : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
-// 16-byte async copy; with valid = false nothing is read and the 16 bytes are zero-filled
-__device__ __forceinline__ void cp16z(void* smem, const void* gmem, bool valid) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    const int n = valid ? 16 : 0;
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(s), "l"(gmem), "r"(n) : "memory");
-}
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
-
 __device__ __forceinline__ uint32_t ld32(const bf16* p) { return *reinterpret_cast<const uint32_t*>(p); }
-
-template <int BN>
-__global__ void __launch_bounds__(256) conv3_fwd_kernel(const bf16* __restrict__ X, int ldx, int cin,
-                                                        const bf16* __restrict__ Wt, int cout,
-                                                        bf16* __restrict__ Y, int ldy, int D, int H, int W,
-                                                        int relu) {
-    __shared__ __align__(16) bf16 As[2][kBM * kPitch];
-    __shared__ __align__(16) bf16 Bs[2][BN * kPitch];
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, gid = lane >> 2, tig = lane & 3;
-    const int V = D * H * W;
-    const int v0 = blockIdx.x * kBM;
-    const int n0 = blockIdx.y * BN;
-    const int nc = cin / 16;
-    const int S = 27 * nc;
-    // copy role: voxel row am, channel half ah
-    const int am = tid >> 1, ah = tid & 1;
-    const int av = v0 + am;
-    const bool avalid = av < V;
-    int az = 0, ay = 0, ax = 0;
-    if (avalid) {
-        az = av / (H * W);
-        const int rr = av - az * H * W;
-        ay = rr / W;
-        ax = rr - ay * W;
-    }
-    auto issue = [&](int s, int buf) {
-        const int t = s / nc, c0 = (s - t * nc) * 16;
-        const int z = az + t / 9 - 1, y = ay + (t / 3) % 3 - 1, x = ax + t % 3 - 1;
-        const bool ok = avalid && z >= 0 && z < D && y >= 0 && y < H && x >= 0 && x < W;
-        const bf16* src = ok ? X + ((size_t)((z * H + y) * W + x) * ldx + c0 + ah * 8) : X;
-        cp16z(&As[buf][am * kPitch + ah * 8], src, ok);
-        for (int q = tid; q < 2 * BN; q += 256) {
-            const int n = q >> 1, hh = q & 1;
-            cp16z(&Bs[buf][n * kPitch + hh * 8], Wt + ((size_t)(t * cout + n0 + n) * cin + c0 + hh * 8), true);
-        }
-        cp_commit();
-    };
-    float acc[BN / 8][4];
-#pragma unroll
-    for (int i = 0; i < BN / 8; i++) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
-    issue(0, 0);
-    for (int s = 0; s < S; s++) {
-        if (s + 1 < S) {
-            issue(s + 1, (s + 1) & 1);
-            cp_wait<1>();
-        } else {
-            cp_wait<0>();
-        }
-        __syncthreads();
-        const bf16* A = As[s & 1] + warp * 16 * kPitch;
-        uint32_t a[4];
-        a[0] = ld32(A + gid * kPitch + 2 * tig);
-        a[1] = ld32(A + (gid + 8) * kPitch + 2 * tig);
-        a[2] = ld32(A + gid * kPitch + 2 * tig + 8);
-        a[3] = ld32(A + (gid + 8) * kPitch + 2 * tig + 8);
-        const bf16* Bb = Bs[s & 1];
-#pragma unroll
-        for (int nt = 0; nt < BN / 8; nt++) {
-            uint32_t b[2];
-            b[0] = ld32(Bb + (nt * 8 + gid) * kPitch + 2 * tig);
-            b[1] = ld32(Bb + (nt * 8 + gid) * kPitch + 2 * tig + 8);
-            mma16816(acc[nt], a, b);
-        }
-        __syncthreads();
-    }
-    const int r0 = v0 + warp * 16 + gid, r1 = r0 + 8;
-#pragma unroll
-    for (int nt = 0; nt < BN / 8; nt++) {
-        const int co = n0 + nt * 8 + 2 * tig;
-        float c0 = acc[nt][0], c1 = acc[nt][1], c2 = acc[nt][2], c3 = acc[nt][3];
-        if (relu) {
-            c0 = fmaxf(c0, 0.f);
-            c1 = fmaxf(c1, 0.f);
-            c2 = fmaxf(c2, 0.f);
-            c3 = fmaxf(c3, 0.f);
-        }
-        if (r0 < V) *reinterpret_cast<__nv_bfloat162*>(Y + (size_t)r0 * ldy + co) = __floats2bfloat162_rn(c0, c1);
-        if (r1 < V) *reinterpret_cast<__nv_bfloat162*>(Y + (size_t)r1 * ldy + co) = __floats2bfloat162_rn(c2, c3);
-    }
-}
 
 // partial[chunk][t][co][ci] = sum over the chunk's voxels v of dY[v][co] X[v + off_t][ci]
 // Both operands are staged transposed ([channel][voxel], 32 voxels per stage, row pitch 40 BF16 =
@@ -392,22 +301,22 @@ pat_status pat_unet_conv3(const void* x, int32_t ldx, int32_t cin, const void* w
     if (cout < 16 || cout > 1024 || cout % 16) return bad("pat_unet_conv3: cout must be a multiple of 16 (<= 1024)");
     if (D < 1 || H < 1 || W < 1 || (int64_t)D * H * W > (1LL << 30)) return bad("pat_unet_conv3: bad volume");
     if (!al16(x) || !al16(w) || !al16(y)) return bad("pat_unet_conv3: pointers must be 16-byte aligned");
-    const int V = D * H * W;
-    const cudaStream_t st = (cudaStream_t)stream;
-    const bf16* X = (const bf16*)x;
-    const bf16* Wt = (const bf16*)w;
-    bf16* Y = (bf16*)y;
-    const unsigned gx = (unsigned)((V + kBM - 1) / kBM);
-    // output-channel tile: the largest of 128, 64, 32, 16 that divides cout
-    if (cout % 128 == 0)
-        conv3_fwd_kernel<128><<<dim3(gx, cout / 128), 256, 0, st>>>(X, ldx, cin, Wt, cout, Y, ldy, D, H, W, relu);
-    else if (cout % 64 == 0)
-        conv3_fwd_kernel<64><<<dim3(gx, cout / 64), 256, 0, st>>>(X, ldx, cin, Wt, cout, Y, ldy, D, H, W, relu);
-    else if (cout % 32 == 0)
-        conv3_fwd_kernel<32><<<dim3(gx, cout / 32), 256, 0, st>>>(X, ldx, cin, Wt, cout, Y, ldy, D, H, W, relu);
-    else
-        conv3_fwd_kernel<16><<<dim3(gx, cout / 16), 256, 0, st>>>(X, ldx, cin, Wt, cout, Y, ldy, D, H, W, relu);
-    return launched("pat_unet_conv3");
+    const cudaError_t e = pat::conv3_tc(x, ldx, cin, w, cout, y, ldy, D, H, W, relu, (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return pat::set_cuda_error(e, "pat_unet_conv3");
+    }
+    return PAT_OK;
+}
+
+pat_status pat_unet_device_status(void* stream) {
+    int word = 0;
+    const cudaError_t e = pat::unet_take_status(&word, (cudaStream_t)stream);
+    if (e != cudaSuccess) return pat::set_cuda_error(e, "pat_unet_device_status");
+    if (word) return pat::set_error(PAT_ERR_TIMEOUT, "pat_unet_device_status: a tensor-core convolution gave up "
+                                                     "waiting for its copies or its matrix multiplies");
+    pat::set_error(PAT_OK, "");
+    return PAT_OK;
 }
 
 int64_t pat_unet_wgrad_scratch(int32_t cin, int32_t cout, int32_t D, int32_t H, int32_t W) {

@@ -85,6 +85,41 @@ def test_conv3_forward_and_data_gradient(dev, cin, cout, dims):
     assert rel(from_dev_cl(dxd, cin, D, H, W), xr.grad) < 4e-3
 
 
+@pytest.mark.parametrize("cin,cout,dims,ldx,ldy", [(16, 16, (3, 5, 7), 48, 32), (32, 256, (4, 4, 8), 32, 256),
+                                                   (512, 16, (2, 2, 2), 512, 16), (64, 32, (16, 32, 32), 96, 48),
+                                                   (16, 16, (5, 3, 200), 16, 16)])
+def test_conv3_channel_slices_odd_volumes_and_wide_layers(dev, cin, cout, dims, ldx, ldy):
+    """Inputs and outputs as channel slices of wider buffers (the U-Net's concatenations), volumes that
+    do not fill a 128-voxel tile or have odd sides, several output-channel tiles (cout 256), the widest
+    input (cin 512), and a volume of many tiles; the device status word stays clean."""
+    from oracle import unet as ou
+    from paper_1605_00133_gb300 import _lib
+    L = _lib.load()
+    D, H, W = dims
+    V = D * H * W
+    x = bf16_exact((cin, D, H, W), 7)
+    w32 = (torch.randn((27, cout, cin), generator=torch.Generator().manual_seed(8)) / (27 * cin) ** 0.5).float()
+    wq = w32.to(torch.bfloat16).double()
+    y_ref = ou.conv3(x, wq)
+    st = torch.cuda.current_stream().cuda_stream
+    off_x, off_y = ldx - cin, ldy - cout  # the slice sits at the end of each row
+    xbuf = torch.full((V, ldx), float("nan"), dtype=torch.bfloat16, device=dev)
+    xbuf[:, off_x:] = to_dev_cl(x)
+    w32d = w32.cuda()
+    wb = torch.empty((27, cout, cin), dtype=torch.bfloat16, device=dev)
+    wt = torch.empty((27, cin, cout), dtype=torch.bfloat16, device=dev)
+    _lib.check(L.pat_unet_cast_weights(w32d.data_ptr(), cin, cout, wb.data_ptr(), wt.data_ptr(), st))
+    ybuf = torch.full((V, ldy), 7.0, dtype=torch.bfloat16, device=dev)
+    _lib.check(L.pat_unet_conv3(xbuf.data_ptr() + 2 * off_x, ldx, cin, wb.data_ptr(), cout,
+                                ybuf.data_ptr() + 2 * off_y, ldy, D, H, W, 1, st))
+    _lib.check(L.pat_unet_device_status(st))
+    got = ybuf[:, off_y:].double().cpu().reshape(D, H, W, cout).permute(3, 0, 1, 2)
+    assert rel(got, torch.relu(y_ref)) < 4e-3
+    assert bool((ybuf[:, :off_y] == 7.0).all())  # nothing outside the slice is written
+    # the NaN channels outside the input slice are never read
+    assert bool(torch.isfinite(ybuf.float()).all())
+
+
 @pytest.mark.parametrize("cin,cout,dims", [(16, 16, (16, 16, 16)), (192, 64, (4, 8, 8)), (64, 128, (2, 4, 4)),
                                            (48, 16, (8, 8, 40)), (32, 32, (3, 5, 7))])
 def test_conv3_weight_gradient(dev, cin, cout, dims):

@@ -11,9 +11,9 @@
  *   of a wider buffer is passed as base + offset with the buffer's ld).  Channel counts and strides
  *   are multiples of 16 and pointers 16-byte aligned.  Convolutions are 3x3x3, stride 1, zero
  *   padding 1, no bias; weights are [27][Cout][Cin] (tap t = 9 (dz+1) + 3 (dy+1) + (dx+1)).
- *   Tensor cores: BF16 operands with FP32 accumulation; the convolution (and with transposed
- *   weights its data gradient) on tcgen05 with tensor-memory accumulators and TMA-staged operands,
- *   the weight gradient on mma.sync m16n8k16.  All calls are ordered on the given stream and return
+ *   Tensor cores: BF16 operands with FP32 accumulation, tcgen05 with tensor-memory accumulators and
+ *   TMA-staged operands, for the convolution, its data gradient (the convolution with transposed
+ *   weights) and its weight gradient.  All calls are ordered on the given stream and return
  *   without synchronising; invalid arguments return PAT_ERR_INVALID_ARG before anything is
  *   launched.
  */
@@ -42,9 +42,10 @@ pat_status pat_unet_device_status(void* cuda_stream);
 
 /* Weight gradient of pat_unet_conv3: dw[t][co][ci] = sum_v dy[v][co] x[v + off_t][ci] (FP32,
  * overwritten), dy the gradient at the convolution's output (after the activation's backward);
- * cin in 16..256, cout in 16..128 (multiples of 16), (cout/16) (cin/8) <= 128.
- * partial: FP32 scratch of at least pat_unet_wgrad_scratch(...) floats; deterministic (fixed-order
- * two-stage reduction). */
+ * cin in 16..256, cout in 16..128 (multiples of 16), strides multiples of 16.  One GEMM over all
+ * taps (rows t cin + ci, columns co, reduction over voxels) split over voxel chunks.
+ * partial: FP32 scratch of at least pat_unet_wgrad_scratch(...) floats, 16-byte aligned;
+ * deterministic (fixed-order sum of the chunks).  Bounded waits as pat_unet_conv3. */
 int64_t pat_unet_wgrad_scratch(int32_t cin, int32_t cout, int32_t D, int32_t H, int32_t W);
 pat_status pat_unet_conv3_wgrad(const void* x, int32_t ldx, int32_t cin, const void* dy, int32_t ldy,
                                 int32_t cout, int32_t D, int32_t H, int32_t W, float* partial, float* dw,

@@ -1,12 +1,7 @@
 // pat_unet.cu - layers of the learned warm start (a 3D U-Net mapping A^T C^T f to a starting image
-// for the TV-Bregman solver): the C ABI of the 3x3x3 convolutions (forward and data gradient on the
-// tcgen05 tensor cores, pat_unet_tc.cu), their weight gradients (BF16 operands, FP32 accumulation,
-// mma.sync m16n8k16), and the elementwise layers around them.
-//
-// Weight gradient: per tap t a GEMM with M = output channels, N = input channels and K = voxels,
-// split over voxel chunks (grid.x) and taps (grid.y), both operands staged transposed in shared
-// memory 32 voxels at a time; the chunk results go to a scratch buffer and a second kernel sums them
-// in a fixed order (deterministic).
+// for the TV-Bregman solver): the C ABI of the 3x3x3 convolutions, their data and weight gradients
+// (on the tcgen05 tensor cores, pat_unet_tc.cu), and the elementwise layers around them (pooling,
+// upsampling, ReLU backward, the input and output layers, the loss and Adam).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -20,115 +15,15 @@ namespace pat {
 cudaError_t conv3_tc(const void* x, int ldx, int cin, const void* w, int cout, void* y, int ldy, int D, int H,
                      int W, int relu, cudaStream_t st);
 cudaError_t unet_take_status(int* word, cudaStream_t st);
+int64_t wgrad_tc_scratch(int cin, int cout, int D, int H, int W);
+cudaError_t wgrad_tc(const void* x, int ldx, int cin, const void* dy, int ldy, int cout, int D, int H, int W,
+                     float* partial, float* dw, cudaStream_t st);
 }  // namespace pat
 
 namespace {
 
 typedef __nv_bfloat16 bf16;
 
-constexpr int kChunk = 2048; // voxels per weight-gradient CTA
-
-__device__ __forceinline__ void mma16816(float* d, const uint32_t* a, const uint32_t* b) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-__device__ __forceinline__ uint32_t ld32(const bf16* p) { return *reinterpret_cast<const uint32_t*>(p); }
-
-// partial[chunk][t][co][ci] = sum over the chunk's voxels v of dY[v][co] X[v + off_t][ci]
-// Both operands are staged transposed ([channel][voxel], 32 voxels per stage, row pitch 40 BF16 =
-// 80 bytes: conflict-free fragment loads); a thread moves one 8-channel vector of one voxel (one
-// 16-byte load, one neighbour computation) and scatters it down a column, consecutive lanes taking
-// consecutive voxels, so each scattered store instruction covers 64 contiguous bytes.
-constexpr int kWTiles = 16;   // mma tiles per warp (M/16 x N/8 <= 8 * 16)
-constexpr int kWV = 32;       // voxels per stage
-constexpr int kWPitch = 40;   // staged row pitch (BF16)
-__global__ void __launch_bounds__(256) conv3_wgrad_kernel(const bf16* __restrict__ X, int ldx, int cin,
-                                                          const bf16* __restrict__ dY, int ldy, int cout,
-                                                          int D, int H, int W, float* __restrict__ partial) {
-    __shared__ __align__(16) bf16 At[128 * kWPitch];  // [co][32 voxels]
-    __shared__ __align__(16) bf16 Bt[256 * kWPitch];  // [ci][32 voxels]
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, gid = lane >> 2, tig = lane & 3;
-    const int V = D * H * W;
-    const int t = blockIdx.y;
-    const int oz = t / 9 - 1, oy = (t / 3) % 3 - 1, ox = t % 3 - 1;
-    const int vbeg = blockIdx.x * kChunk, vend = min(V, vbeg + kChunk);
-    const int NT8 = cin / 8, ntiles = (cout / 16) * NT8;
-    const int ncot = cout / 8, ncit = cin / 8;  // 8-channel vectors per voxel
-    float acc[kWTiles][4];
-#pragma unroll
-    for (int i = 0; i < kWTiles; i++) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
-    for (int vb = vbeg; vb < vend; vb += kWV) {
-        for (int q = tid; q < kWV * ncot; q += 256) {
-            const int kk = q % kWV, ch = q / kWV;
-            const int v = vb + kk;
-            uint4 w = make_uint4(0, 0, 0, 0);
-            if (v < vend) w = *reinterpret_cast<const uint4*>(dY + (size_t)v * ldy + 8 * ch);
-            const bf16* e = reinterpret_cast<const bf16*>(&w);
-#pragma unroll
-            for (int j = 0; j < 8; j++) At[(8 * ch + j) * kWPitch + kk] = e[j];
-        }
-        for (int q = tid; q < kWV * ncit; q += 256) {
-            const int kk = q % kWV, ch = q / kWV;
-            const int v = vb + kk;
-            uint4 w = make_uint4(0, 0, 0, 0);
-            if (v < vend) {
-                const int z = v / (H * W), rr = v - z * H * W, y = rr / W, x = rr - y * W;
-                const int zz = z + oz, yy = y + oy, xx = x + ox;
-                if (zz >= 0 && zz < D && yy >= 0 && yy < H && xx >= 0 && xx < W)
-                    w = *reinterpret_cast<const uint4*>(X + (size_t)((zz * H + yy) * W + xx) * ldx + 8 * ch);
-            }
-            const bf16* e = reinterpret_cast<const bf16*>(&w);
-#pragma unroll
-            for (int j = 0; j < 8; j++) Bt[(8 * ch + j) * kWPitch + kk] = e[j];
-        }
-        __syncthreads();
-#pragma unroll
-        for (int k0 = 0; k0 < kWV; k0 += 16) {
-#pragma unroll
-            for (int i = 0; i < kWTiles; i++) {
-                const int tile = warp + 8 * i;
-                if (tile < ntiles) {
-                    const int mt = tile / NT8, nt = tile - mt * NT8;
-                    const bf16* A = At + mt * 16 * kWPitch + k0;
-                    uint32_t a[4], b[2];
-                    a[0] = ld32(A + gid * kWPitch + 2 * tig);
-                    a[1] = ld32(A + (gid + 8) * kWPitch + 2 * tig);
-                    a[2] = ld32(A + gid * kWPitch + 2 * tig + 8);
-                    a[3] = ld32(A + (gid + 8) * kWPitch + 2 * tig + 8);
-                    const bf16* Bb = Bt + (nt * 8 + gid) * kWPitch + k0;
-                    b[0] = ld32(Bb + 2 * tig);
-                    b[1] = ld32(Bb + 2 * tig + 8);
-                    mma16816(acc[i], a, b);
-                }
-            }
-        }
-        __syncthreads();
-    }
-    float* out = partial + ((size_t)blockIdx.x * 27 + t) * cout * cin;
-#pragma unroll
-    for (int i = 0; i < kWTiles; i++) {
-        const int tile = warp + 8 * i;
-        if (tile < ntiles) {
-            const int mt = tile / NT8, nt = tile - mt * NT8;
-            const int co = mt * 16 + gid, ci = nt * 8 + 2 * tig;
-            out[(size_t)co * cin + ci] = acc[i][0];
-            out[(size_t)co * cin + ci + 1] = acc[i][1];
-            out[(size_t)(co + 8) * cin + ci] = acc[i][2];
-            out[(size_t)(co + 8) * cin + ci + 1] = acc[i][3];
-        }
-    }
-}
-
-__global__ void sum_chunks_kernel(const float* __restrict__ partial, int nchunk, long long n, float* __restrict__ out) {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        float s = 0.f;
-        for (int c = 0; c < nchunk; c++) s += partial[(size_t)c * n + i];
-        out[i] = s;
-    }
-}
 
 __global__ void cast_weights_kernel(const float* __restrict__ w32, int cin, int cout, bf16* __restrict__ wb,
                                     bf16* __restrict__ wt) {
@@ -320,28 +215,24 @@ pat_status pat_unet_device_status(void* stream) {
 }
 
 int64_t pat_unet_wgrad_scratch(int32_t cin, int32_t cout, int32_t D, int32_t H, int32_t W) {
-    const int64_t V = (int64_t)D * H * W;
-    const int64_t nchunk = (V + kChunk - 1) / kChunk;
-    return nchunk * 27 * (int64_t)cin * cout;
+    if (cin < 16 || cout < 16 || D < 1 || H < 1 || W < 1) return 0;
+    return pat::wgrad_tc_scratch(cin, cout, D, H, W);
 }
 
 pat_status pat_unet_conv3_wgrad(const void* x, int32_t ldx, int32_t cin, const void* dy, int32_t ldy, int32_t cout,
                                 int32_t D, int32_t H, int32_t W, float* partial, float* dw, void* stream) {
     if (!x || !dy || !partial || !dw) return bad("pat_unet_conv3_wgrad: NULL pointer");
-    if (cin < 16 || cin > 256 || cin % 16 || ldx < cin || ldx % 8 || ldy < cout || ldy % 8 || cout < 16 ||
+    if (cin < 16 || cin > 256 || cin % 16 || ldx < cin || ldx % 16 || ldy < cout || ldy % 16 || cout < 16 ||
         cout > 128 || cout % 16)
-        return bad("pat_unet_conv3_wgrad: cin in 16..256 and cout in 16..128, multiples of 16");
-    if (!al16(x) || !al16(dy)) return bad("pat_unet_conv3_wgrad: pointers must be 16-byte aligned");
-    if ((cout / 16) * (cin / 8) > 8 * kWTiles) return bad("pat_unet_conv3_wgrad: cin * cout too large");
+        return bad("pat_unet_conv3_wgrad: cin in 16..256 and cout in 16..128, multiples of 16; strides too");
+    if (!al16(x) || !al16(dy) || !al16(partial)) return bad("pat_unet_conv3_wgrad: pointers must be 16-byte aligned");
     if (D < 1 || H < 1 || W < 1 || (int64_t)D * H * W > (1LL << 30)) return bad("pat_unet_conv3_wgrad: bad volume");
-    const int V = D * H * W;
-    const int nchunk = (V + kChunk - 1) / kChunk;
-    const cudaStream_t st = (cudaStream_t)stream;
-    conv3_wgrad_kernel<<<dim3(nchunk, 27), 256, 0, st>>>((const bf16*)x, ldx, cin, (const bf16*)dy, ldy, cout, D, H, W,
-                                                         partial);
-    const long long n = 27LL * cin * cout;
-    sum_chunks_kernel<<<grid_for(n), 256, 0, st>>>(partial, nchunk, n, dw);
-    return launched("pat_unet_conv3_wgrad");
+    const cudaError_t e = pat::wgrad_tc(x, ldx, cin, dy, ldy, cout, D, H, W, partial, dw, (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return pat::set_cuda_error(e, "pat_unet_conv3_wgrad");
+    }
+    return PAT_OK;
 }
 
 pat_status pat_unet_cast_weights(const float* w32, int32_t cin, int32_t cout, void* wb, void* wt, void* stream) {

@@ -120,13 +120,19 @@ def test_conv3_channel_slices_odd_volumes_and_wide_layers(dev, cin, cout, dims, 
     assert bool(torch.isfinite(ybuf.float()).all())
 
 
-@pytest.mark.parametrize("cin,cout,dims", [(16, 16, (16, 16, 16)), (192, 64, (4, 8, 8)), (64, 128, (2, 4, 4)),
-                                           (48, 16, (8, 8, 40)), (32, 32, (3, 5, 7))])
-def test_conv3_weight_gradient(dev, cin, cout, dims):
+@pytest.mark.parametrize("cin,cout,dims,ldx,ldy", [(16, 16, (16, 16, 16), 16, 16), (192, 64, (4, 8, 8), 192, 64),
+                                                   (64, 128, (2, 4, 4), 64, 128), (48, 16, (8, 8, 40), 48, 16),
+                                                   (32, 32, (3, 5, 7), 32, 32), (32, 48, (8, 16, 16), 96, 80),
+                                                   (256, 128, (2, 2, 4), 256, 128), (16, 16, (64, 32, 32), 16, 16)])
+def test_conv3_weight_gradient(dev, cin, cout, dims, ldx, ldy):
+    """All 27 taps' weight gradients against the FP64 reference: FP32 accumulation of exact BF16
+    products (1e-5); channel slices of wider buffers, odd volumes, the widest layer and a volume of
+    many voxel blocks (64x32x32, split over chunks and summed in a fixed order)."""
     from oracle import unet as ou
     from paper_1605_00133_gb300 import _lib
     L = _lib.load()
     D, H, W = dims
+    V = D * H * W
     x = bf16_exact((cin, D, H, W), 4)
     dy = bf16_exact((cout, D, H, W), 5)
     w = torch.zeros((27, cout, cin), dtype=torch.float64, requires_grad=True)
@@ -134,11 +140,16 @@ def test_conv3_weight_gradient(dev, cin, cout, dims):
     st = torch.cuda.current_stream().cuda_stream
     scratch = torch.empty(L.pat_unet_wgrad_scratch(cin, cout, D, H, W), dtype=torch.float32, device=dev)
     dw = torch.empty((27, cout, cin), dtype=torch.float32, device=dev)
-    xd, dyd = to_dev_cl(x), to_dev_cl(dy)
-    _lib.check(L.pat_unet_conv3_wgrad(xd.data_ptr(), cin, cin, dyd.data_ptr(), cout, cout,
-                                      D, H, W, scratch.data_ptr(), dw.data_ptr(), st))
-    torch.cuda.synchronize()
-    assert rel(dw.cpu(), w.grad) < 1e-5
+    xbuf = torch.full((V, ldx), float("nan"), dtype=torch.bfloat16, device=dev)
+    dbuf = torch.full((V, ldy), float("nan"), dtype=torch.bfloat16, device=dev)
+    xbuf[:, ldx - cin:] = to_dev_cl(x)
+    dbuf[:, ldy - cout:] = to_dev_cl(dy)
+    for _ in range(2):  # the scratch keeps the previous call's contents: results must not depend on it
+        _lib.check(L.pat_unet_conv3_wgrad(xbuf.data_ptr() + 2 * (ldx - cin), ldx, cin,
+                                          dbuf.data_ptr() + 2 * (ldy - cout), ldy, cout,
+                                          D, H, W, scratch.data_ptr(), dw.data_ptr(), st))
+        _lib.check(L.pat_unet_device_status(st))
+        assert rel(dw.cpu(), w.grad) < 1e-5
 
 
 def test_pool_up_and_their_backwards(dev):

@@ -41,9 +41,13 @@ def test_trained_warm_start_beats_the_cold_start(dev):
     for e in ev:
         plain = {t["inner"]: t["rel_err"] for t in e["plain"]}
         warm = {t["inner"]: t["rel_err"] for t in e["warm"]}
+        print("plain", plain, "warm", warm)
         assert warm[0] == e["network_rel_err"] and e["network_rel_err"] < 1.0
-        for n in (5, 10):
+        # at every budget the warm-started solve is closer to the converged reconstruction
+        for n in (5, 10, 20, 40):
             assert warm[n] < plain[n], (n, warm, plain)
-        t = e["seconds_to"]["0.1"]
-        assert t["warm"] is not None and (t["plain"] is None or t["warm"] < t["plain"]), t
+        # and it gets as close as the cold start's longest solve in less wall time
+        t_plain = next(t["seconds"] for t in e["plain"] if t["inner"] == 40)
+        t_warm = next(t["seconds"] for t in e["warm"] if t["rel_err"] <= plain[40])
+        assert t_warm < t_plain, (t_warm, t_plain)
     op.close()

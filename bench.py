@@ -35,8 +35,9 @@ if ROOT not in sys.path:
 
 METRIC = "A+A^T pairs/s (64x128x128, 400 steps)"
 
-# (kernel source hash, workload, batch) -> DRAM bytes (read + write) of one time step, from ncu
-STEP_TRAFFIC = {("7a22aba1b07a", "c2", 1): 53.54e6}
+# (kernel source hash, workload, batch) -> DRAM bytes (read + write) of one forward time step (x, y and
+# z passes), from ncu with the L2 as the run leaves it (--cache-control none)
+STEP_TRAFFIC = {("66d6b960a722", "c2", 1): 3.04e6, ("66d6b960a722", "c4", 1): 672.2e6}
 UNIT = "pairs/s"
 
 
@@ -52,6 +53,11 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-solve", action="store_true",
                     help="skip the TV-Bregman reconstruction timing (the `solve` object)")
+    ap.add_argument("--unet", action="store_true",
+                    help="also time the learned warm start's U-Net (inference and one training step) at the "
+                         "workload's grid: its tensor-core convolutions against the BF16 roofline")
+    ap.add_argument("--unet-only", action="store_true",
+                    help="only the U-Net timing (no operator timing, solve or CPU baseline)")
     ap.add_argument("--warm", action="store_true",
                     help="also train the learned warm start and time warm vs plain solves to 2 %% error")
     ap.add_argument("--warm-train", type=int, default=64)
@@ -214,6 +220,10 @@ def main():
     w = presets.workload(args.workload)
     B = args.batch
     g = w.grid
+    if args.unet_only:
+        if rank == 0:
+            print(json.dumps({"metric": "U-Net training steps/s", "unet": unet_experiment(args, g, dev)}), flush=True)
+        return 0
     gb = presets.Grid(g.nz, g.ny, g.nx, dx=g.dx, c=g.c, rho0=g.rho0, cfl=g.cfl, T=g.T,
                       pml_size=g.pml_size, pml_alpha=g.pml_alpha, sensor_z=g.sensor_z, batch=B)
     op = PatOperator(gb, w.sampling)
@@ -289,7 +299,8 @@ def main():
     traffic = STEP_TRAFFIC.get((_source_hash(), w.name, B))
     roofline = {"bound": "hbm", "kernel": "time step (line passes x, y, z of A, and of A^T)",
                 "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "peak_source": peak_src,
+                "traffic": traffic, "traffic_unit": "DRAM bytes (read + write) of one time step, ncu, warm L2",
+                "peak_source": peak_src,
                 "algorithmic_bytes_per_unit": "48 B per voxel per time step",
                 "dominant_kernel": dominant, "dominant_share": kernels[dominant]["share"],
                 "dominant_avg_us": kernels[dominant]["avg_us"]}
@@ -340,6 +351,8 @@ def main():
         solve = solve_experiment(args, op, f, p0, dev)
         op.device_status(dev)
 
+    unet_line = unet_experiment(args, g, dev) if args.unet else None
+
     warm = None
     if args.warm and B == 1:
         warm = warm_start_experiment(args, op, g, dev)
@@ -359,6 +372,8 @@ def main():
             line["solve"] = solve
         if warm is not None:
             line["warm_start"] = warm
+        if unet_line is not None:
+            line["unet"] = unet_line
         print(json.dumps(line), flush=True)
     op.close()
     if dist:
@@ -496,6 +511,56 @@ def cpu_baseline(w):
     out["solve_extrapolated_seconds"] = {"value": 300.0 / v, "note": "about 300 A + A^T pairs (5 x 50 FISTA "
                                          "steps, restarts, 20 power iterations) x the all-core pair time"}
     return out
+
+
+def unet_experiment(args, g, dev):
+    """The U-Net of the learned warm start at the workload's grid: inference and one training step
+    (forward, data and weight gradients of its 14 3x3x3 convolutions, the other layers, Adam), CUDA
+    events around K runs after W warm-up runs, L2 flushed between runs.  Convolution flops: 2 x 27 x
+    cin x cout per voxel for the forward pass, the same again for the data gradient (except the first
+    layer's, which is not needed) and for the weight gradient; peak = the measured BF16 tensor rate
+    (the dense GEMM burst figure of the machine's cuBLAS measurement)."""
+    import torch
+
+    from paper_1605_00133_gb300 import _lib, unet
+    net = unet.WarmStartUNet(g.nz, g.ny, g.nx, seed=0)
+    gen = torch.Generator(device=dev).manual_seed(1)
+    x = torch.randn(g.n, device=dev, generator=gen)
+    t = torch.randn(g.n, device=dev, generator=gen)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
+    fwd = sum(2.0 * 27 * c[0] * c[1] * net.V[c[2]] for c in unet.LAYERS.values())
+    dgrad = fwd - 2.0 * 27 * 16 * 16 * net.V[0]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+            flush.fill_(1.0)
+        torch.cuda.synchronize()
+        total = 0.0
+        for _ in range(args.steps):
+            flush.fill_(1.0)
+            e0.record()
+            fn()
+            e1.record()
+            torch.cuda.synchronize()
+            total += e0.elapsed_time(e1)
+        return total / args.steps
+
+    ms_inf = timed(lambda: net.forward(x))
+    ms_train = timed(lambda: net.train_step(x, t, lr=1e-5))
+    _lib.check(_lib.load().pat_unet_device_status(torch.cuda.current_stream(dev).cuda_stream))
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peak = 1910.0
+    if os.path.exists(peaks_path):
+        peak = float(json.load(open(peaks_path)).get("bf16_tflops", peak))
+    return {"grid": [g.nz, g.ny, g.nx], "inference_ms": ms_inf, "train_step_ms": ms_train,
+            "conv_gflop_inference": fwd / 1e9, "conv_gflop_train_step": (2 * fwd + dgrad) / 1e9,
+            "inference_conv_tflops": fwd / (ms_inf * 1e-3) / 1e12,
+            "train_conv_tflops": (2 * fwd + dgrad) / (ms_train * 1e-3) / 1e12,
+            "bf16_peak_tflops": peak, "peak_source": "measured bf16_tflops (burst)",
+            "note": "whole-step times include the non-convolution layers; the fractions of the peak are "
+                    "lower bounds for the convolution kernels alone"}
 
 
 def warm_start_experiment(args, op, g, dev):

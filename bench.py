@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batch-scan", action="store_true",
+                    help="skip the timing of 2 and 4 volumes per call (the `batch_scan` object)")
     ap.add_argument("--no-solve", action="store_true",
                     help="skip the TV-Bregman reconstruction timing (the `solve` object)")
     ap.add_argument("--unet", action="store_true",
@@ -353,6 +355,36 @@ def main():
 
     unet_line = unet_experiment(args, g, dev) if args.unet else None
 
+    # the same step with 2 and 4 independent volumes per call (volume-pairs/s): B = 1 is the
+    # line's value; these show what batching gains
+    batch_scan = None
+    if B == 1 and world == 1 and not args.no_batch_scan:
+        batch_scan = {"1": value}
+        for nb in (2, 4):
+            gbn = presets.Grid(g.nz, g.ny, g.nx, dx=g.dx, c=g.c, rho0=g.rho0, cfl=g.cfl, T=g.T,
+                               pml_size=g.pml_size, pml_alpha=g.pml_alpha, sensor_z=g.sensor_z, batch=nb)
+            opn = PatOperator(gbn, w.sampling)
+            p0n = torch.tensor(np.stack([w.p0(seed_offset=o) for o in range(nb)]).astype(np.float32), device=dev)
+            fn = torch.empty(opn.data_shape, device=dev)
+            pn = torch.empty(opn.image_shape, device=dev)
+
+            def step_n():
+                opn.forward_into(p0n, fn)
+                opn.adjoint_into(fn, pn)
+                flush.fill_(1.0)
+            for _ in range(args.warmup):
+                step_n()
+            torch.cuda.synchronize()
+            e0.record()
+            for _ in range(args.steps):
+                step_n()
+            e1.record()
+            torch.cuda.synchronize()
+            opn.device_status(dev)
+            batch_scan[str(nb)] = nb * args.steps / (e0.elapsed_time(e1) / 1e3)
+            opn.close()
+            del p0n, fn, pn
+
     warm = None
     if args.warm and B == 1:
         warm = warm_start_experiment(args, op, g, dev)
@@ -374,6 +406,8 @@ def main():
             line["warm_start"] = warm
         if unet_line is not None:
             line["unet"] = unet_line
+        if batch_scan is not None:
+            line["batch_scan"] = {"unit": "volume-pairs/s", "volumes_per_call": batch_scan}
         print(json.dumps(line), flush=True)
     op.close()
     if dist:

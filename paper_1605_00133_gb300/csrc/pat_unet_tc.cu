@@ -257,8 +257,9 @@ __global__ void __launch_bounds__(kThreads, 1) conv3_tc_kernel(const __grid_cons
 
 // ---------------------------------------------------------------------------------------------
 // Weight gradient: dW[t][co][ci] = sum_v dY[v][co] X[v + off_t][ci], all 27 taps in one GEMM with
-// M = (tap, input channel) rows m = t cin + ci, N = output channels and K = voxels, split over chunks
-// of voxel blocks (grid.x) with a fixed-order sum afterwards.  A K block is a box of 64 voxels.  Both
+// M = (tap, input channel) rows m = t cin + ci (M tiles along grid.x, so that the CTAs reading one
+// voxel chunk run together and find its input in L2), N = output channels and K = voxels, split over
+// chunks of voxel blocks (grid.y) with a fixed-order sum afterwards.  A K block is a box of 64 voxels.  Both
 // operands arrive channel-contiguous, i.e. MN-major: a swizzle atom is 8 voxel rows x WA channels of
 // one tap (A) or 8 voxel rows x WB output channels (B), WA, WB in {16, 32, 64}; the M tile's 128 rows
 // are 128 / WA atoms side by side (one TMA box each: the tap's shifted voxel box, zero outside the
@@ -307,8 +308,9 @@ __global__ void __launch_bounds__(kThreads, 1) wgrad_tc_kernel(const __grid_cons
     int* counts = reinterpret_cast<int*>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int mtile = blockIdx.y;
-    const int kb0 = blockIdx.x * a.kb_per_cta;
+    const int mtile = blockIdx.x;  // M tiles fastest: the CTAs of one voxel chunk run together
+    const int chunk = blockIdx.y;
+    const int kb0 = chunk * a.kb_per_cta;
     const int nkb = min(a.kb_per_cta, a.nkb - kb0);
     const int natoms_a = kBM / a.wa;                 // atoms (tap, channel block) of this M tile
     const int cblocks = a.cin / a.wa;
@@ -390,7 +392,7 @@ __global__ void __launch_bounds__(kThreads, 1) wgrad_tc_kernel(const __grid_cons
         tc_fence_after();
         const int m = 32 * (warp & 3) + lane;
         const uint32_t trow = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
-        float* out = a.partial + ((size_t)blockIdx.x * gridDim.y * kBM + (size_t)mtile * kBM + m) * a.cout;
+        float* out = a.partial + ((size_t)chunk * gridDim.x * kBM + (size_t)mtile * kBM + m) * a.cout;
         for (int c = 0; c < a.cout; c += 16) {
             float v[16];
             tc_ld16(trow + (uint32_t)c, v);
@@ -619,7 +621,7 @@ cudaError_t wgrad_tc(const void* x, int ldx, int cin, const void* dy, int ldy, i
     if (smem < floor_smem) smem = floor_smem;
     cudaError_t e = cudaFuncSetAttribute(wgrad_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    wgrad_tc_kernel<<<dim3((unsigned)g.nchunk, (unsigned)g.mtiles), kThreads, smem, st>>>(mx, md, a);
+    wgrad_tc_kernel<<<dim3((unsigned)g.mtiles, (unsigned)g.nchunk), kThreads, smem, st>>>(mx, md, a);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const long long n = 27LL * cin * cout;

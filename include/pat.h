@@ -175,6 +175,12 @@ typedef struct {
     double step_scale;      /* eta = step_scale / L (> 0) */
     int32_t max_backtrack;  /* step halvings after a restart (>= 0) */
     int32_t stall;          /* early stop after this many steps without a new minimum of E (>= 1) */
+    /* Checkpoint / resume of the Bregman iteration (device pointers, FP64 [T][m], or NULL): the state
+     * between Bregman steps is the image p and the Bregman variable b.  b_in replaces b^0 = 0 (pass
+     * the image as warm_dev); b_out receives b after the last step.  A solve of K1 + K2 steps equals a
+     * solve of K1 steps followed by one of K2 steps resumed from its image and b_out. */
+    const double* b_in;
+    double* b_out;
 } pat_solve_params;
 
 typedef struct {

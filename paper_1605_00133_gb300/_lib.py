@@ -51,7 +51,8 @@ class SolveParams(ctypes.Structure):
     _fields_ = [("lambda_", ctypes.c_double), ("outer", ctypes.c_int32), ("inner", ctypes.c_int32),
                 ("prox_iters", ctypes.c_int32), ("L", ctypes.c_double), ("power_iters", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("step_scale", ctypes.c_double),
-                ("max_backtrack", ctypes.c_int32), ("stall", ctypes.c_int32)]
+                ("max_backtrack", ctypes.c_int32), ("stall", ctypes.c_int32),
+                ("b_in", ctypes.c_void_p), ("b_out", ctypes.c_void_p)]
 
 
 class SolveReport(ctypes.Structure):

@@ -459,6 +459,7 @@ pat_status pat_grid_info(const pat_grid* G, int64_t* n_image, int64_t* n_data, i
 int64_t pat_workspace_bytes(const pat_grid* G) { return G ? G->bytes : 0; }
 
 pat_status pat_forward(pat_grid* G, const float* p0, float* f, void* stream) {
+    const NvtxRange range("pat_forward");
     g_err.clear();
     if (!G) return fail(PAT_ERR_INVALID_ARG, "pat_forward: NULL grid");
     if (!p0 || (!f && G->m > 0)) return fail(PAT_ERR_INVALID_ARG, "pat_forward: NULL buffer");
@@ -470,6 +471,7 @@ pat_status pat_forward(pat_grid* G, const float* p0, float* f, void* stream) {
 }
 
 pat_status pat_adjoint(pat_grid* G, const float* f, float* p, void* stream) {
+    const NvtxRange range("pat_adjoint");
     g_err.clear();
     if (!G) return fail(PAT_ERR_INVALID_ARG, "pat_adjoint: NULL grid");
     if (!p || (!f && G->m > 0)) return fail(PAT_ERR_INVALID_ARG, "pat_adjoint: NULL buffer");
@@ -627,6 +629,7 @@ void* g_noalloc_ptr[64] = {nullptr};  // device address of g_noalloc_scratch, pe
 }  // namespace
 
 extern "C" pat_status pat_forward_noalloc(pat_grid* G, const float* p0, float* f, void* stream) {
+    const NvtxRange range("pat_forward_noalloc");
     g_err.clear();
     if (!G) return fail(PAT_ERR_INVALID_ARG, "pat_forward_noalloc: NULL grid");
     if (!p0 || (!f && G->m > 0)) return fail(PAT_ERR_INVALID_ARG, "pat_forward_noalloc: NULL buffer");

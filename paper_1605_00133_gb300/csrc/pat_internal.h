@@ -1,6 +1,7 @@
 // pat_internal.h - host-side structures shared by the C ABI layer and the kernel launchers.
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 #include <vector>
@@ -109,6 +110,15 @@ struct Scalars {
 // Kernel classes timed by the optional profiler (CUDA events on the launching stream).
 enum KernelClass {
     KC_LINE_X = 0, KC_LINE_Y, KC_LINE_Z, KC_PLANE_FFT, KC_Z_FFT, KC_SAMPLE, KC_COUNT
+};
+
+// NVTX range over a scope (for tracing tools such as Nsight Systems; a no-op when none is attached):
+// the C-ABI calls, the time loops and the solver's Bregman steps are ranges.
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
 struct Profiler {

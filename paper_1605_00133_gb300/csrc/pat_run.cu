@@ -280,6 +280,7 @@ cudaError_t run_forward(const Geom& g, const DeviceTables& t, const Workspace& w
             la[ax].s_mid = (float)(1.0 / g.len[ax]);
             la[ax].s_post = (float)c2;
         }
+        const NvtxRange loop("forward time loop");
         for (int n = 0; n + 1 < g.T; n++) {
             float2* cur = w.ph[n & 1];
             float2* nxt = w.ph[(n + 1) & 1];
@@ -346,6 +347,7 @@ cudaError_t run_adjoint(const Geom& g, const DeviceTables& t, const Workspace& w
         la[ax].s_post = (float)(s.dt / s.rho0);
     }
     int cur = 0;
+    const NvtxRange loop("adjoint time loop");
     for (int n = g.T - 2; n >= 0; n--) {
         for (int ax : kPassOrder) {
             LineArgs& a = la[ax];

@@ -450,6 +450,7 @@ using namespace pat;
 
 extern "C" pat_status pat_tv_prox(pat_grid* G, const float* in, float* out, double alpha, int32_t iters,
                                   int32_t bc, void* stream) {
+    const NvtxRange range("pat_tv_prox");
     set_error(PAT_OK, "");
     if (!G) return set_error(PAT_ERR_INVALID_ARG, "pat_tv_prox: NULL grid");
     if (!in || !out) return set_error(PAT_ERR_INVALID_ARG, "pat_tv_prox: NULL buffer");
@@ -475,6 +476,7 @@ extern "C" pat_status pat_tv_prox(pat_grid* G, const float* in, float* out, doub
 
 extern "C" pat_status pat_bp_tv(pat_grid* G, const float* f, float* p_out, double alpha, int32_t iters,
                                 void* stream) {
+    const NvtxRange range("pat_bp_tv");
     set_error(PAT_OK, "");
     if (!G) return set_error(PAT_ERR_INVALID_ARG, "pat_bp_tv: NULL grid");
     if (!p_out || (!f && G->m > 0)) return set_error(PAT_ERR_INVALID_ARG, "pat_bp_tv: NULL buffer");
@@ -497,6 +499,7 @@ extern "C" pat_status pat_bp_tv(pat_grid* G, const float* f, float* p_out, doubl
 
 extern "C" pat_status pat_bregman_solve(pat_grid* G, const float* f, const float* warm, float* p_out,
                                         const pat_solve_params* params, pat_solve_report* report, void* stream) {
+    const NvtxRange range("pat_bregman_solve");
     set_error(PAT_OK, "");
     if (!G || !params) return set_error(PAT_ERR_INVALID_ARG, "pat_bregman_solve: NULL grid or params");
     if (!f || !p_out) return set_error(PAT_ERR_INVALID_ARG, "pat_bregman_solve: NULL buffer");
@@ -525,8 +528,11 @@ extern "C" pat_status pat_bregman_solve(pat_grid* G, const float* f, const float
     const double eta = P.step_scale / L;
     if (warm) PAT_CUDA(cudaMemcpyAsync(w.xp, warm, c.N * sizeof(float), cudaMemcpyDeviceToDevice, c.st), "warm start");
     else PAT_CUDA(cudaMemsetAsync(w.xp, 0, c.N * sizeof(float), c.st), "cold start");
-    PAT_CUDA(cudaMemsetAsync(w.bdat, 0, c.D * sizeof(double), c.st), "Bregman init");
+    if (P.b_in) PAT_CUDA(cudaMemcpyAsync(w.bdat, P.b_in, c.D * sizeof(double), cudaMemcpyDeviceToDevice, c.st),
+                         "Bregman resume");
+    else PAT_CUDA(cudaMemsetAsync(w.bdat, 0, c.D * sizeof(double), c.st), "Bregman init");
     for (int k = 0; k < P.outer; k++) {
+        const NvtxRange step("Bregman step");
         data_shift_kernel<<<ew_blocks(c.D), 256, 0, c.st>>>(w.gdat, f, w.bdat, c.D);
         PAT_CUDA(cudaGetLastError(), "data launch");
         FistaOut fo;
@@ -549,6 +555,9 @@ extern "C" pat_status pat_bregman_solve(pat_grid* G, const float* f, const float
         rep.n_residual = std::min(k + 1, 64);
     }
     PAT_CUDA(cudaMemcpyAsync(p_out, w.xp, c.N * sizeof(float), cudaMemcpyDeviceToDevice, c.st), "solution copy");
+    if (P.b_out)
+        PAT_CUDA(cudaMemcpyAsync(P.b_out, w.bdat, c.D * sizeof(double), cudaMemcpyDeviceToDevice, c.st),
+                 "Bregman state copy");
     if (report) *report = rep;
     // a time-step kernel whose bounded wait for a bulk copy gave up makes every result since then
     // undefined; the solve has synchronised anyway, so it reads (and clears) the record itself

@@ -150,16 +150,24 @@ class PatOperator:
     def bregman_solve(self, f: torch.Tensor, lam: float, outer: int = 5, inner: int = 50,
                       prox_iters: int = 100, L: float = 0.0, power_iters: int = 20, seed: int = 0,
                       step_scale: float = 1.8, max_backtrack: int = 5, stall: int = 5,
-                      warm: torch.Tensor = None, out: torch.Tensor = None):
-        """TV+ (outer = 1) or TV+Br reconstruction from data f (pat_bregman_solve).
-        Returns (p, report dict)."""
+                      warm: torch.Tensor = None, out: torch.Tensor = None, b_in: torch.Tensor = None,
+                      b_out: torch.Tensor = None):
+        """TV+ (outer = 1) or TV+Br reconstruction from data f (pat_bregman_solve).  b_in / b_out:
+        float64 device tensors of the data's shape, the Bregman variable to resume from / saved after
+        the last step (with warm = the image, a checkpoint of the solve).  Returns (p, report dict)."""
+        for name, b in (("b_in", b_in), ("b_out", b_out)):
+            if b is not None and (b.dtype != torch.float64 or not b.is_cuda or not b.is_contiguous()
+                                  or b.numel() != int(np.prod(self.data_shape))):
+                raise ValueError(f"{name} must be a contiguous CUDA float64 tensor of shape {self.data_shape}")
         self._check_tensor(f, self.data_shape, "f")
         if warm is not None:
             self._check_tensor(warm, self.image_shape, "warm")
         if out is None:
             out = torch.empty(self.image_shape, device=f.device, dtype=torch.float32)
         P = _lib.SolveParams(float(lam), int(outer), int(inner), int(prox_iters), float(L), int(power_iters),
-                             int(seed), float(step_scale), int(max_backtrack), int(stall))
+                             int(seed), float(step_scale), int(max_backtrack), int(stall),
+                             b_in.data_ptr() if b_in is not None else None,
+                             b_out.data_ptr() if b_out is not None else None)
         R = _lib.SolveReport()
         _lib.check(_lib.load().pat_bregman_solve(self._h, f.data_ptr(), warm.data_ptr() if warm is not None else None,
                                                  out.data_ptr(), ctypes.byref(P), ctypes.byref(R),

@@ -414,3 +414,38 @@ def test_device_status_is_clean_after_forward_and_adjoint(dev):
         op.adjoint(y)
         op.device_status(dev)
         op.close()
+
+
+def test_calls_write_only_their_outputs(dev):
+    """Canaries: outputs as the head of larger buffers filled with a sentinel, inputs compared after
+    the call.  Forward, adjoint, C, C^T and the prox write exactly their outputs and leave their
+    inputs untouched (rSP and sHd grids, batch 2)."""
+    from paper_1605_00133_gb300 import _lib
+    L = _lib.load()
+    st = torch.cuda.current_stream(dev).cuda_stream
+    for kind in (presets.KIND_RSP, presets.KIND_SHD01):
+        g = presets.Grid(16, 16, 32, T=7, pml_size=3, batch=2)
+        s = presets.make_sampling(g, kind, 96, 4)
+        op = make_op(g, s)
+        nimg, ndat = 2 * g.n, 2 * g.T * s.m
+        x = torch.rand(nimg, device=dev)
+        x0 = x.clone()
+        fbuf = torch.full((ndat + 4096,), 12345.0, device=dev)
+        _lib.check(L.pat_forward(op._h, x.data_ptr(), fbuf.data_ptr(), st))
+        y = torch.randn(ndat, device=dev)
+        y0 = y.clone()
+        pbuf = torch.full((nimg + 4096,), 12345.0, device=dev)
+        _lib.check(L.pat_adjoint(op._h, y.data_ptr(), pbuf.data_ptr(), st))
+        plane = torch.rand(2 * 3 * g.m_plane, device=dev)
+        cbuf = torch.full((2 * 3 * s.m + 4096,), 12345.0, device=dev)
+        _lib.check(L.pat_sample(op._h, plane.data_ptr(), cbuf.data_ptr(), 3, st))
+        tbuf = torch.full((2 * 3 * g.m_plane + 4096,), 12345.0, device=dev)
+        _lib.check(L.pat_sample_adjoint(op._h, cbuf.data_ptr(), tbuf.data_ptr(), 3, st))
+        qbuf = torch.full((nimg + 4096,), 12345.0, device=dev)
+        _lib.check(L.pat_tv_prox(op._h, x.data_ptr(), qbuf.data_ptr(), 0.05, 10, 0, st))
+        torch.cuda.synchronize()
+        for buf, n in ((fbuf, ndat), (pbuf, nimg), (cbuf, 2 * 3 * s.m), (tbuf, 2 * 3 * g.m_plane), (qbuf, nimg)):
+            assert bool((buf[n:] == 12345.0).all())
+            assert bool(torch.isfinite(buf[:n]).all()) and not bool((buf[:n] == 12345.0).any())
+        assert torch.equal(x, x0) and torch.equal(y, y0)
+        op.close()

@@ -141,3 +141,22 @@ def test_c2_bregman_residual_decreases(dev):
     assert float(p.min()) >= 0.0
     err = float((p - p0).norm() / p0.norm())
     assert err < 1.0
+
+
+def test_bregman_solve_checkpoint_and_resume(dev, c1_problem):
+    """A solve of 4 Bregman steps equals 2 steps, a checkpoint (the image and the Bregman variable
+    b_out), then 2 more steps resumed from it (warm = the image, b_in = b): bit for bit, since the
+    resumed solve runs the same operations on the same data."""
+    g, s, _, f = c1_problem
+    op = op_for(g, s)
+    ft = torch.tensor(f, dtype=torch.float32, device=dev).reshape(op.data_shape)
+    _, rep = op.bregman_solve(ft, 1e-3, outer=1, inner=1, prox_iters=1, power_iters=10)
+    kw = dict(inner=5, prox_iters=20, L=rep["L"])
+    p4, r4 = op.bregman_solve(ft, 1e-3, outer=4, **kw)
+    b = torch.full(op.data_shape, float("nan"), dtype=torch.float64, device=dev)
+    p2, _ = op.bregman_solve(ft, 1e-3, outer=2, b_out=b, **kw)
+    assert bool(torch.isfinite(b).all())
+    p22, r22 = op.bregman_solve(ft, 1e-3, outer=2, warm=p2.clone(), b_in=b, **kw)
+    assert torch.equal(p22, p4)
+    assert r22["residuals"] == r4["residuals"][2:]
+    op.close()

@@ -40,6 +40,13 @@ pat_status pat_unet_conv3(const void* x, int32_t ldx, int32_t cin, const void* w
  * convolutions since the last check are invalid). */
 pat_status pat_unet_device_status(void* cuda_stream);
 
+/* Test hook for that failure path (no counterpart in the paper), process-wide: while
+ * stop_after_stage >= 0, the convolutions (pat_unet_conv3) issue the TMA copies of only their first
+ * stop_after_stage K steps and give up waiting for the next after `polls` polls (0: the default);
+ * nothing is left in flight, each CTA frees its tensor memory and exits, the outputs are invalid and
+ * pat_unet_device_status reports PAT_ERR_TIMEOUT.  stop_after_stage = -1 restores normal operation. */
+pat_status pat_unet_debug_copy_fault(int32_t stop_after_stage, int32_t polls);
+
 /* Weight gradient of pat_unet_conv3: dw[t][co][ci] = sum_v dy[v][co] x[v + off_t][ci] (FP32,
  * overwritten), dy the gradient at the convolution's output (after the activation's backward);
  * cin in 16..256, cout in 16..128 (multiples of 16), strides multiples of 16.  One GEMM over all

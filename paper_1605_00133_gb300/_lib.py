@@ -24,7 +24,7 @@ EXPORTS = ["pat_create_grid", "pat_destroy_grid", "pat_grid_info", "pat_workspac
 UNET_EXPORTS = ["pat_unet_conv3", "pat_unet_wgrad_scratch", "pat_unet_conv3_wgrad", "pat_unet_cast_weights",
                 "pat_unet_relu_bwd", "pat_unet_pool", "pat_unet_pool_bwd_add", "pat_unet_up", "pat_unet_up_bwd",
                 "pat_unet_input", "pat_unet_head", "pat_unet_head_scratch", "pat_unet_head_bwd", "pat_unet_adam",
-                "pat_unet_device_status"]
+                "pat_unet_device_status", "pat_unet_debug_copy_fault"]
 
 
 class PatError(RuntimeError):
@@ -133,6 +133,7 @@ def load() -> ctypes.CDLL:
         L.pat_unet_head_bwd.argtypes = [vp, vp, vp, vp, i64, vp, vp, vp, vp, vp]
         L.pat_unet_adam.argtypes = [vp, vp, vp, vp, i64, f32, f32, f32, f32, i32, vp]
         L.pat_unet_device_status.argtypes = [vp]
+        L.pat_unet_debug_copy_fault.argtypes = [i32, i32]
         for name in UNET_EXPORTS:
             if name not in ("pat_unet_wgrad_scratch", "pat_unet_head_scratch"):
                 getattr(L, name).restype = ctypes.c_int

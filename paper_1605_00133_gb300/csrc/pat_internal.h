@@ -79,7 +79,7 @@ struct DeviceTables {
     // j + 2 [j >= len/2])
     float2* pass[PS_COUNT][3];
     int* err;                   // one word: bulk copies of the line passes that never landed (bits)
-    int polls;                  // poll limit of the line passes' bounded waits (1 << 20 by default)
+    int polls;                  // poll limit of the waits for copies the test hook leaves out
     int skip;                   // test hook (pat_debug_copy_fault): state copies not issued (bits 1, 2)
 };
 

@@ -87,7 +87,7 @@ struct LineArgs {
     const float* c2[3];         // state 2
     const float2* tabs;         // LM_STEP: all the tables above in one block (DeviceTables::pass)
     int* err;                   // device word: bit i set when bulk copy i of a pass never landed
-    int polls;                  // poll limit of each bounded wait for a bulk copy
+    int polls;                  // poll limit of the waits for the copies `skip` leaves out
     int skip;                   // fault-injection hook for tests: bulk copies (bits 1, 2) not issued
     float2* rec;                // z lines: plane spectrum recorded this step (LF_RECORD) ...
     const float2* inj;          // ... or injected this step (LF_INJECT); batch stride plane_bs

@@ -59,6 +59,8 @@
 
 namespace pat {
 
+constexpr int kCopyPolls = 1 << 20;  // bound of a wait for a bulk copy: each poll suspends <= ~1 us
+
 template <int L>
 struct LS {
     static constexpr int A = Split<L>::A;  // radix of the spatial-side DFT
@@ -462,16 +464,20 @@ struct LineCtx {
         }
         cp_async_commit();
     }
-    // wait for bulk copy i, bounded by a.polls polls; a copy that has not landed by then is recorded
-    // in a.err (bit i) and reported as false, and the caller does not use its tile
+    // wait for bulk copy i, bounded (kCopyPolls polls, about a second; a copy the test hook left out,
+    // a.skip bit i, only a.polls); a copy that has not landed by then is recorded in a.err (bit i) and
+    // reported as false, and the caller does not use its tile
     __device__ __forceinline__ bool wait_copy(int i) const {
-        if (mbar_wait(bar + i, 0, a.polls)) return true;
+        if (mbar_wait(bar + i, 0, (a.skip & (1 << i)) ? a.polls : kCopyPolls)) return true;
         atomicOr(a.err, 1 << i);
         return false;
     }
-    // before exiting after a wait gave up: wait once more, bounded, so that a copy that was only late
-    // lands before this CTA's shared memory can be handed to another CTA
-    __device__ __forceinline__ void drain(int i) const { mbar_wait(bar + i, 0, a.polls); }
+    // before exiting after a wait gave up: wait once more, with the same bound, so that a copy that
+    // was only late lands before this CTA's shared memory can be handed to another CTA (a copy the
+    // test hook left out was never issued: nothing is in flight)
+    __device__ __forceinline__ void drain(int i) const {
+        mbar_wait(bar + i, 0, (a.skip & (1 << i)) ? a.polls : kCopyPolls);
+    }
 
     // cp.async copy of the old output of z and y lines into pfo (one commit group, committed by every
     // thread; issue only after the output's writer has completed)

@@ -15,6 +15,7 @@ namespace pat {
 cudaError_t conv3_tc(const void* x, int ldx, int cin, const void* w, int cout, void* y, int ldy, int D, int H,
                      int W, int relu, cudaStream_t st);
 cudaError_t unet_take_status(int* word, cudaStream_t st);
+void unet_set_copy_fault(int stop_after, int polls);
 int64_t wgrad_tc_scratch(int cin, int cout, int D, int H, int W);
 cudaError_t wgrad_tc(const void* x, int ldx, int cin, const void* dy, int ldy, int cout, int D, int H, int W,
                      float* partial, float* dw, cudaStream_t st);
@@ -201,6 +202,13 @@ pat_status pat_unet_conv3(const void* x, int32_t ldx, int32_t cin, const void* w
         cudaGetLastError();
         return pat::set_cuda_error(e, "pat_unet_conv3");
     }
+    return PAT_OK;
+}
+
+pat_status pat_unet_debug_copy_fault(int32_t stop_after_stage, int32_t polls) {
+    if (stop_after_stage < -1 || polls < 0) return bad("pat_unet_debug_copy_fault: stop_after_stage >= -1, polls >= 0");
+    pat::unet_set_copy_fault(stop_after_stage, polls);
+    pat::set_error(PAT_OK, "");
     return PAT_OK;
 }
 

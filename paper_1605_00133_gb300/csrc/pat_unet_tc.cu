@@ -39,6 +39,10 @@ constexpr int kBM = 128;
 constexpr int kThreads = 192;
 constexpr int kPolls = 1 << 20;  // bounded waits: each poll suspends for at most about a microsecond
 
+// test hook of the convolution's failure path (pat_unet_debug_copy_fault): process-wide
+int g_stop_after = -1;
+int g_polls = kPolls;
+
 struct ConvTcArgs {
     __nv_bfloat16* y;
     int ldy, cin, cout, bn;
@@ -47,6 +51,8 @@ struct ConvTcArgs {
     int tx, ty;         // tiles along x and y
     int relu;
     uint32_t tmem_cols;
+    int stop_after;     // test hook: the producer issues only stages < stop_after (< 0: all)
+    int polls;          // poll limit of the wait for the first stage the test hook leaves out
 };
 
 // shared-memory matrix descriptor of a K-major operand tile: rows of `row_bytes` (= the swizzle
@@ -169,6 +175,7 @@ __global__ void __launch_bounds__(kThreads, 1) conv3_tc_kernel(const __grid_cons
         int s = 0;
         for (; s < S; s++) {
             const int st = s % kNStage, use = s / kNStage;
+            if (a.stop_after >= 0 && s >= a.stop_after) break;  // test hook: nothing more is issued
             if (use > 0 && !mbar_wait(empty + st, (use - 1) & 1, kPolls)) {
                 counts[2] = 1;
                 break;
@@ -187,7 +194,9 @@ __global__ void __launch_bounds__(kThreads, 1) conv3_tc_kernel(const __grid_cons
         int s = 0;
         for (; s < S; s++) {
             const int st = s % kNStage, use = s / kNStage;
-            if (!mbar_wait(full + st, use & 1, kPolls)) {
+            // the test hook's short limit applies only to the first stage it leaves out
+            const int lim = (a.stop_after >= 0 && s >= a.stop_after) ? a.polls : kPolls;
+            if (!mbar_wait(full + st, use & 1, lim)) {
                 counts[2] = 1;
                 break;
             }
@@ -500,6 +509,8 @@ cudaError_t conv3_tc(const void* x, int ldx, int cin, const void* w, int cout, v
     if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
     a.relu = relu;
     a.tmem_cols = a.bn < 32 ? 32 : a.bn;
+    a.stop_after = g_stop_after;
+    a.polls = g_polls;
     const CUtensorMapSwizzle swz =
         ck == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : ck == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B;
     alignas(64) CUtensorMap mx, mw;
@@ -628,6 +639,13 @@ cudaError_t wgrad_tc(const void* x, int ldx, int cin, const void* dy, int ldy, i
     const int blocks = (int)((n + 255) / 256 < 152 * 8 ? (n + 255) / 256 : 152 * 8);
     wgrad_sum_kernel<<<blocks, 256, 0, st>>>(partial, g.nchunk, g.mtiles * kBM, cin, cout, dw);
     return cudaGetLastError();
+}
+
+// test hook: later convolutions issue only their first stop_after stages (< 0: normal operation) and
+// give up waiting after `polls` polls (<= 0: the default)
+void unet_set_copy_fault(int stop_after, int polls) {
+    g_stop_after = stop_after;
+    g_polls = polls > 0 ? polls : kPolls;
 }
 
 // reads and clears the device word of the tensor-core convolutions

@@ -62,3 +62,48 @@ def test_a_copy_that_never_lands_is_reported_and_the_context_survives(dev, oracl
     assert rel(back.double().cpu().numpy().reshape(g.shape), oracle_mod.adjoint(g, s, y)) < 1e-5
     op.device_status(dev)
     op.close()
+
+
+def test_tensor_core_convolution_gives_up_cleanly(dev):
+    """pat_unet_debug_copy_fault makes the tcgen05 convolution issue only its first three K steps: the
+    MMA thread's bounded wait for the fourth gives up, the CTA frees its tensor memory and exits, and
+    pat_unet_device_status reports PAT_ERR_TIMEOUT once.  With the hook off the same convolutions
+    (and a large one over many tiles, which needs tensor memory on every SM) give the results of
+    before, bit for bit."""
+    from paper_1605_00133_gb300 import _lib
+    lib = _lib.load()
+    st = torch.cuda.current_stream(dev).cuda_stream
+    g = torch.Generator(device=dev).manual_seed(0)
+
+    def conv(D, H, W, cin, cout):
+        x = torch.randn((D * H * W, cin), device=dev, generator=g).to(torch.bfloat16)
+        w = (0.1 * torch.randn((27, cout, cin), device=dev, generator=g)).to(torch.bfloat16)
+        y = torch.zeros((D * H * W, cout), dtype=torch.bfloat16, device=dev)
+        return x, w, y
+
+    small = conv(8, 8, 8, 32, 32)
+    large = conv(32, 64, 64, 16, 16)
+    ref = []
+    for x, w, y in (small, large):
+        _lib.check(lib.pat_unet_conv3(x.data_ptr(), x.shape[1], x.shape[1], w.data_ptr(), y.shape[1],
+                                      y.data_ptr(), y.shape[1], *((8, 8, 8) if x is small[0] else (32, 64, 64)),
+                                      0, st))
+        ref.append(y.clone())
+    _lib.check(lib.pat_unet_device_status(st))
+    x, w, y = small
+    try:
+        _lib.check(lib.pat_unet_debug_copy_fault(3, 4))
+        _lib.check(lib.pat_unet_conv3(x.data_ptr(), 32, 32, w.data_ptr(), 32, y.data_ptr(), 32, 8, 8, 8, 0, st))
+        with pytest.raises(_lib.PatError) as e:
+            _lib.check(lib.pat_unet_device_status(st))
+        assert e.value.status == 4
+    finally:
+        _lib.check(lib.pat_unet_debug_copy_fault(-1, 0))
+    _lib.check(lib.pat_unet_device_status(st))  # cleared
+    for (x, w, y), r, dims in ((small, ref[0], (8, 8, 8)), (large, ref[1], (32, 64, 64))):
+        y.zero_()
+        _lib.check(lib.pat_unet_conv3(x.data_ptr(), x.shape[1], x.shape[1], w.data_ptr(), y.shape[1],
+                                      y.data_ptr(), y.shape[1], *dims, 0, st))
+        torch.cuda.synchronize()
+        assert torch.equal(y, r)
+    _lib.check(lib.pat_unet_device_status(st))

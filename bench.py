@@ -467,6 +467,7 @@ def solve_experiment(args, op, f_clean, p0, dev):
         if ladder[-1]["rel_err_vs_ref"] <= 0.02:
             break
     t2 = next((e["seconds"] for e in ladder if e["rel_err_vs_ref"] <= 0.02), None)
+    prox_rate = prox_timing(op, prec, lam * 1.8 / L, prox)
     seconds_to = {f"{tol:g}": next((e["seconds"] for e in ladder if e["rel_err_vs_ref"] <= tol), None)
                   for tol in (0.10, 0.05, 0.02)}
     return {"seconds": secs, "reconstructions_per_min": 60.0 / secs, "outer": wl.bregman_outer,
@@ -477,9 +478,38 @@ def solve_experiment(args, op, f_clean, p0, dev):
             "reference": {"inner": 300, "prox_iters": prox, "fista_iterations": rref["inner_total"],
                           "seconds": t_ref},
             "plain_seconds_to_2pct": t2, "plain_seconds_to": seconds_to, "ladder": ladder,
+            "prox": prox_rate,
             "warm_start": "plain cold-start solve; bench.py --warm trains the learned U-Net warm start and "
                           "times warm against plain against a 5 x 600 reference (the line's warm_start "
                           "object; about 35 GPU-minutes with 128 training phantoms)"}
+
+
+def prox_timing(op, x, alpha, iters, reps=5):
+    """The TV prox alone at the solver's alpha = eta lam: CUDA events around `reps` calls of `iters`
+    fused primal-dual iterations (one launch each; a call's initial clamp and dual reset included).
+    Algorithmic bytes per voxel and iteration: qbar, the three dual components, q and the input
+    read, the dual, q and qbar written, 11 x 4 B = 44 B."""
+    import json as _json
+
+    import torch
+    out = torch.empty_like(x)
+    op.tv_prox(x, alpha, iters, out=out)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        op.tv_prox(x, alpha, iters, out=out)
+    e1.record()
+    torch.cuda.synchronize()
+    us = e0.elapsed_time(e1) * 1e3 / (reps * iters)
+    voxels = x.numel()
+    gbs = 44.0 * voxels / (us * 1e-6) / 1e9
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peak = float(_json.load(open(peaks_path))["hbm_gbs"]) if os.path.exists(peaks_path) else 6800.0
+    return {"iters": iters, "us_per_iter": us, "voxels": voxels, "algorithmic_bytes_per_voxel": 44,
+            "achieved_gbs": gbs, "frac_of_hbm": gbs / peak,
+            "note": "one launch per iteration; the prox's fields (11 image-sized FP32 arrays) stay in L2 "
+                    "at this size, so the fraction is of the HBM copy bandwidth, not DRAM traffic"}
 
 
 def cpu_model():

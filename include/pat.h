@@ -147,7 +147,8 @@ pat_status pat_sample_adjoint(pat_grid* grid, const float* f_dev, float* pbar_de
  * values return PAT_ERR_UNSUPPORTED).  Solved by `iters` steps of the accelerated primal-dual
  * hybrid gradient method (tau_0 = sigma_0 = 1/sqrt(12), theta = 1/sqrt(1 + 2 tau)), started at
  * q = max(0, in).  in_dev / out_dev: float[B][Nz][Ny][Nx]; they may alias.  The first call on a
- * grid allocates its prox workspace (4 image-sized FP32 buffers). */
+ * grid allocates its prox workspace (9 image-sized FP32 buffers: the input copy, and the dual
+ * variable (3) and over-relaxed iterate read from one set and written to the other). */
 pat_status pat_tv_prox(pat_grid* grid, const float* in_dev, float* out_dev, double alpha, int32_t iters,
                        int32_t bc, void* cuda_stream);
 

@@ -162,7 +162,7 @@ cudaError_t run_sample_adjoint(const Geom& g, const Workspace& w, int kind, int 
 struct SolverWs {
     size_t n_img = 0, n_dat = 0;  // per-call sizes the buffers were made for
     float *x = nullptr, *xp = nullptr, *y = nullptr, *z = nullptr, *grad = nullptr;  // image, B*N
-    float *qbar = nullptr, *xi = nullptr;                                          // prox: N, 3N
+    float *qbar = nullptr, *qbar2 = nullptr, *xi = nullptr, *xi2 = nullptr;         // prox: N, N, 3N, 3N
     float *ax = nullptr, *axp = nullptr, *ay = nullptr, *r = nullptr;              // data, T*m
     double *gdat = nullptr, *bdat = nullptr;                                        // data, FP64
     double *partial = nullptr, *result = nullptr;                                   // reductions

@@ -2,9 +2,9 @@
 //
 //   pat_tv_prox        argmin_{q >= 0} 1/2 ||q - p||^2 + alpha TV(q), TV isotropic with forward
 //                      differences and Neumann boundary (App. A), by the accelerated primal-dual
-//                      hybrid gradient method the paper names (App. B): one dual kernel (ball
-//                      projection of xi + sigma grad(qbar)) and one primal kernel (divergence, data
-//                      term and the non-negativity clamp fused) per iteration; step sizes follow
+//                      hybrid gradient method the paper names (App. B): one launch per iteration,
+//                      the dual step (ball projection of xi + sigma grad(qbar)) fused with the
+//                      primal step (divergence, data term, non-negativity clamp); step sizes follow
 //                      theta = 1/sqrt(1 + 2 tau), tau <- theta tau, sigma <- sigma / theta,
 //                      tau_0 = sigma_0 = 1/sqrt(12).
 //   pat_bregman_solve  Bregman iterations (Eqs. BregIterA/B) around an accelerated proximal-gradient
@@ -71,7 +71,7 @@ __global__ void clamp_copy_kernel(float* __restrict__ q, float* __restrict__ qba
     }
 }
 
-// ------------------------------------------------------------------------------ TV prox kernels
+// ------------------------------------------------------------------------------ TV prox kernel
 
 struct TvDims {
     int nz, ny, nx;
@@ -79,48 +79,145 @@ struct TvDims {
     size_t total;  // B*n
 };
 
-// xi <- project_{|.| <= alpha}(xi + sigma grad(qbar)); forward differences, zero past the last voxel
-__global__ void tv_dual_kernel(float* __restrict__ xz, float* __restrict__ xy, float* __restrict__ xx,
-                               const float* __restrict__ qb, float sigma, float alpha, TvDims d) {
-    const size_t plane = (size_t)d.ny * d.nx;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < d.total; i += (size_t)gridDim.x * blockDim.x) {
-        const size_t v = i % d.n;
-        const int x = (int)(v % d.nx), y = (int)((v / d.nx) % d.ny), z = (int)(v / plane);
-        const float c = qb[i];
-        const float gz = (z + 1 < d.nz) ? qb[i + plane] - c : 0.f;
-        const float gy = (y + 1 < d.ny) ? qb[i + d.nx] - c : 0.f;
-        const float gx = (x + 1 < d.nx) ? qb[i + 1] - c : 0.f;
-        const float a = fmaf(sigma, gz, xz[i]), b = fmaf(sigma, gy, xy[i]), e = fmaf(sigma, gx, xx[i]);
-        const float nrm = sqrtf(a * a + b * b + e * e);
-        const float s = (nrm > alpha) ? alpha / nrm : 1.f;
-        xz[i] = a * s;
-        xy[i] = b * s;
-        xx[i] = e * s;
-    }
+// One primal-dual iteration per launch, dual and primal steps fused (App. B):
+//   xi'   = project_{|.| <= alpha}(xi + sigma grad(qbar))        dual, every voxel
+//   q'    = max(0, (q - tau grad^T(xi') + tau p) / (1 + tau))    primal, the clamp fused
+//   qbar' = q' + theta (q' - q)
+// grad: forward differences, zero past the last voxel of an axis; grad^T(xi)(v) = sum over axes of
+// [xi_a(v - e_a) if v has a predecessor] - [xi_a(v) if v has a successor].
+// A CTA owns a 32 x kTvRows tile of (x, y) columns over a run of z planes and marches along z:
+// lanes are consecutive x, warps consecutive y, and warp 0 is the halo row y0 - 1, whose new dual
+// the first output row needs.  The x neighbours come by warp shuffle (lane 31 loads qbar at
+// x0 + 32, lane 0 also evaluates the dual at x0 - 1), the y neighbours through shared memory, and
+// the new dual's z component of the plane below stays in a register; a run's first plane needs
+// the plane before it, which the CTA evaluates first without storing it.  qbar and xi are read from
+// one buffer and written to the other (neighbouring CTAs read the old values); q is read and
+// written only at its own voxel.
+constexpr int kTvRows = 8;
+constexpr int kTvWarps = kTvRows + 1;
+
+struct TvStep {
+    const float* qb_in;
+    float* qb_out;
+    const float* xi_in;  // components z, y, x at offsets 0, N, 2N
+    float* xi_out;
+    float* q;
+    const float* p;
+    float sigma, alpha, tau, theta;
+    int nonneg;
+    int nz, ny, nx;
+    int zrun, nruns;  // planes per run, runs per image
+    long long n, N;   // voxels per image, B * n
+};
+
+__device__ __forceinline__ void tv_project(float& a, float& b, float& e, float alpha) {
+    const float nrm = sqrtf(a * a + b * b + e * e);
+    const float s = (nrm > alpha) ? alpha / nrm : 1.f;
+    a *= s;
+    b *= s;
+    e *= s;
 }
 
-// q_new = max(0, (q - tau grad^T xi + tau p) / (1 + tau)), qbar = q_new + theta (q_new - q)
-// grad^T xi at v = sum_axes [xi(v - e) if v has a predecessor] - [xi(v) if v has a successor]
-__global__ void tv_primal_kernel(float* __restrict__ q, float* __restrict__ qb, const float* __restrict__ xz,
-                                 const float* __restrict__ xy, const float* __restrict__ xx,
-                                 const float* __restrict__ p, float tau, float theta, int nonneg, TvDims d) {
-    const size_t plane = (size_t)d.ny * d.nx;
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < d.total; i += (size_t)gridDim.x * blockDim.x) {
-        const size_t v = i % d.n;
-        const int x = (int)(v % d.nx), y = (int)((v / d.nx) % d.ny), z = (int)(v / plane);
-        float gt = 0.f;
-        if (z + 1 < d.nz) gt -= xz[i];
-        if (z > 0) gt += xz[i - plane];
-        if (y + 1 < d.ny) gt -= xy[i];
-        if (y > 0) gt += xy[i - d.nx];
-        if (x + 1 < d.nx) gt -= xx[i];
-        if (x > 0) gt += xx[i - 1];
-        const float q0 = q[i];
-        float qn = fmaf(-tau, gt, fmaf(tau, p[i], q0)) / (1.f + tau);
-        if (nonneg) qn = fmaxf(0.f, qn);
-        q[i] = qn;
-        qb[i] = fmaf(theta, qn - q0, qn);
-    }
+// what a thread reads for plane z (its qbar at z itself is carried from the plane before)
+struct TvIn {
+    float qn;          // qbar at z + 1
+    float xz, xy, xx;  // dual at the own voxel
+    float qv, pv;      // q and the prox input (output voxels only)
+    float qr, qd;      // qbar at x0 + 32 (lane 31) and at y + 1 (last warp)
+    float qln, qld;    // lane 0 of the output rows: qbar at (z + 1, y, x0 - 1) and (z, y + 1, x0 - 1)
+    float lz, ly, lx;  //   and the dual at (z, y, x0 - 1)
+};
+
+__global__ void __launch_bounds__(32 * kTvWarps) tv_step_kernel(TvStep a) {
+    __shared__ float sq[kTvWarps][32];  // qbar of the current plane, one row per warp
+    __shared__ float sy[kTvWarps][32];  // y component of the new dual, one row per warp
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int x0 = blockIdx.x * 32, x = x0 + lane;
+    const int y = blockIdx.y * kTvRows - 1 + w;
+    const int b = blockIdx.z / a.nruns, run = blockIdx.z - b * a.nruns;
+    const int z0 = run * a.zrun, z1 = min(z0 + a.zrun, a.nz);
+    const bool yin = y >= 0 && y < a.ny, in = yin && x < a.nx;
+    const bool own = in && w > 0;                               // writes its voxel (planes z0 .. z1-1)
+    const bool xn = x + 1 < a.nx, yn = y + 1 < a.ny;            // voxel has a successor along x / y
+    const bool halo = lane == 0 && x0 > 0 && yin && w > 0;      // evaluates the dual at x0 - 1
+    const bool right = lane == 31 && x0 + 32 < a.nx && yin;     // loads qbar at x0 + 32
+    const bool down = w == kTvWarps - 1 && in && yn;            // loads qbar at y + 1
+    const long long plane = (long long)a.ny * a.nx;
+    const long long base = b * a.n + (long long)y * a.nx + x;   // + z * plane; dereferenced only when in
+    const float* __restrict__ qb = a.qb_in;
+    const float* __restrict__ xi = a.xi_in;
+    auto load = [&](int z) {
+        TvIn v;
+        const long long o = base + z * plane;
+        const bool zn = z + 1 < a.nz, store = own && z >= z0;
+        v.qn = (in && zn) ? qb[o + plane] : 0.f;
+        v.xz = in ? xi[o] : 0.f;
+        v.xy = in ? xi[a.N + o] : 0.f;
+        v.xx = in ? xi[2 * a.N + o] : 0.f;
+        v.qv = store ? a.q[o] : 0.f;
+        v.pv = store ? a.p[o] : 0.f;
+        v.qr = right ? qb[o + 1] : 0.f;
+        v.qd = down ? qb[o + a.nx] : 0.f;
+        v.qln = (halo && zn) ? qb[o - 1 + plane] : 0.f;
+        v.qld = (halo && yn) ? qb[o - 1 + a.nx] : 0.f;
+        v.lz = halo ? xi[o - 1] : 0.f;
+        v.ly = halo ? xi[a.N + o - 1] : 0.f;
+        v.lx = halo ? xi[2 * a.N + o - 1] : 0.f;
+        return v;
+    };
+    const int zs = z0 > 0 ? z0 - 1 : z0;
+    float qc = in ? qb[base + zs * plane] : 0.f;         // qbar at (z, y, x)
+    float qlc = halo ? qb[base - 1 + zs * plane] : 0.f;  // qbar at (z, y, x0 - 1)
+    float pz = 0.f;                                      // z component of the new dual at z - 1
+    // plane z from its reads `cur`.  The reads are not issued a plane ahead: a CTA barrier waits
+    // for the loads in flight, so reads issued before the barriers of the plane before would
+    // only add registers (measured slower).
+    auto step = [&](int z, const TvIn& cur) {
+        const long long o = base + z * plane;
+        const bool zn = z + 1 < a.nz, store = own && z >= z0;
+        sq[w][lane] = qc;
+        __syncthreads();
+        // new dual at the own voxel
+        const float qxn = __shfl_down_sync(0xffffffffu, qc, 1);
+        const float qyn = (w < kTvWarps - 1) ? sq[w + 1][lane] : cur.qd;
+        const float gz = zn ? cur.qn - qc : 0.f;
+        const float gy = yn ? qyn - qc : 0.f;
+        const float gx = xn ? (lane < 31 ? qxn : cur.qr) - qc : 0.f;
+        float dz = fmaf(a.sigma, gz, cur.xz), dy = fmaf(a.sigma, gy, cur.xy), dx = fmaf(a.sigma, gx, cur.xx);
+        tv_project(dz, dy, dx, a.alpha);
+        // new dual at x0 - 1 (lane 0 of the output rows): only its x component is used
+        float dlx = 0.f;
+        if (halo) {
+            float ez = fmaf(a.sigma, zn ? cur.qln - qlc : 0.f, cur.lz);
+            float ey = fmaf(a.sigma, yn ? cur.qld - qlc : 0.f, cur.ly);
+            float ex = fmaf(a.sigma, qc - qlc, cur.lx);
+            tv_project(ez, ey, ex, a.alpha);
+            dlx = ex;
+        }
+        sy[w][lane] = dy;
+        __syncthreads();
+        const float dxl = __shfl_up_sync(0xffffffffu, dx, 1);
+        if (store) {
+            float gt = 0.f;
+            if (zn) gt -= dz;
+            if (z > 0) gt += pz;
+            if (yn) gt -= dy;
+            if (y > 0) gt += sy[w - 1][lane];
+            if (xn) gt -= dx;
+            if (x > 0) gt += lane > 0 ? dxl : dlx;
+            float qnew = fmaf(-a.tau, gt, fmaf(a.tau, cur.pv, cur.qv)) / (1.f + a.tau);
+            if (a.nonneg) qnew = fmaxf(0.f, qnew);
+            a.q[o] = qnew;
+            a.qb_out[o] = fmaf(a.theta, qnew - cur.qv, qnew);
+            a.xi_out[o] = dz;
+            a.xi_out[a.N + o] = dy;
+            a.xi_out[2 * a.N + o] = dx;
+        }
+        pz = dz;
+        qc = cur.qn;
+        qlc = cur.qln;
+    };
+    for (int z = zs; z < z1; z++) step(z, load(z));
 }
 
 // ------------------------------------------------------------------------------ FP64 reductions
@@ -144,8 +241,9 @@ __device__ __forceinline__ double red_term(const RedArgs& r, size_t i) {
         }
         case RED_TV: {
             const size_t plane = (size_t)r.d.ny * r.d.nx;
-            const size_t v = i % r.d.n;
-            const int x = (int)(v % r.d.nx), y = (int)((v / r.d.nx) % r.d.ny), z = (int)(v / plane);
+            const unsigned v = (unsigned)(i % r.d.n), nx = (unsigned)r.d.nx, ny = (unsigned)r.d.ny;
+            const unsigned t = v / nx;
+            const int x = (int)(v - t * nx), y = (int)(t % ny), z = (int)(t / ny);
             const double c = r.a[i];
             const double gz = (z + 1 < r.d.nz) ? (double)r.a[i + plane] - c : 0.0;
             const double gy = (y + 1 < r.d.ny) ? (double)r.a[i + r.d.nx] - c : 0.0;
@@ -222,7 +320,9 @@ static pat_status ensure_ws(pat_grid* G, bool solver) {
     pat_status st = PAT_OK;
     if (!w.qbar) {
         st = grid_alloc(G, (void**)&w.qbar, N * sizeof(float), "prox qbar");
+        if (st == PAT_OK) st = grid_alloc(G, (void**)&w.qbar2, N * sizeof(float), "prox qbar");
         if (st == PAT_OK) st = grid_alloc(G, (void**)&w.xi, 3 * N * sizeof(float), "prox dual");
+        if (st == PAT_OK) st = grid_alloc(G, (void**)&w.xi2, 3 * N * sizeof(float), "prox dual");
         if (st == PAT_OK) st = grid_alloc(G, (void**)&w.z, N * sizeof(float), "prox input copy");
         if (st == PAT_OK) st = grid_alloc(G, (void**)&w.partial, kRedBlocks * sizeof(double), "reduction");
         if (st == PAT_OK) st = grid_alloc(G, (void**)&w.result, sizeof(double), "reduction");
@@ -257,19 +357,46 @@ static pat_status tv_prox_run(Ctx& c, const float* p, float* q, double alpha, in
     clamp_copy_kernel<<<nb, 256, 0, c.st>>>(q, w.qbar, p, c.N);
     if (!nonneg) PAT_CUDA(cudaMemcpyAsync(q, p, c.N * sizeof(float), cudaMemcpyDeviceToDevice, c.st), "prox init");
     if (!nonneg) PAT_CUDA(cudaMemcpyAsync(w.qbar, p, c.N * sizeof(float), cudaMemcpyDeviceToDevice, c.st), "prox init");
-    if (alpha <= 0.0) {
+    if (alpha <= 0.0 || iters == 0) {
         PAT_CUDA(cudaGetLastError(), "prox launch");
         return PAT_OK;
     }
     PAT_CUDA(cudaMemsetAsync(w.xi, 0, 3 * c.N * sizeof(float), c.st), "prox init");
+    const TvDims& d = c.td;
+    const int B = (int)(d.total / d.n);
+    const int gx = (d.nx + 31) / 32, gy = (d.ny + kTvRows - 1) / kTvRows;
+    // runs of z planes: about 512 CTAs in all, at least 4 planes per run (each run evaluates one
+    // plane more than it stores)
+    const long long cols = (long long)gx * gy * B;
+    int nruns = (int)std::max<long long>(1, std::min<long long>((512 + cols - 1) / cols, (d.nz + 3) / 4));
+    const int zrun = (d.nz + nruns - 1) / nruns;
+    nruns = (d.nz + zrun - 1) / zrun;
+    TvStep a;
+    a.q = q;
+    a.p = p;
+    a.alpha = (float)alpha;
+    a.nonneg = nonneg;
+    a.nz = d.nz;
+    a.ny = d.ny;
+    a.nx = d.nx;
+    a.zrun = zrun;
+    a.nruns = nruns;
+    a.n = (long long)d.n;
+    a.N = (long long)d.total;
+    const dim3 grid(gx, gy, B * nruns);
+    float* qb[2] = {w.qbar, w.qbar2};
+    float* xi[2] = {w.xi, w.xi2};
     double tau = 1.0 / sqrt(12.0), sigma = 1.0 / (tau * 12.0);
-    float* xz = w.xi;
-    float* xy = w.xi + c.N;
-    float* xx = w.xi + 2 * c.N;
     for (int it = 0; it < iters; it++) {
         const double theta = 1.0 / sqrt(1.0 + 2.0 * tau);
-        tv_dual_kernel<<<nb, 256, 0, c.st>>>(xz, xy, xx, w.qbar, (float)sigma, (float)alpha, c.td);
-        tv_primal_kernel<<<nb, 256, 0, c.st>>>(q, w.qbar, xz, xy, xx, p, (float)tau, (float)theta, nonneg, c.td);
+        a.qb_in = qb[it & 1];
+        a.qb_out = qb[(it + 1) & 1];
+        a.xi_in = xi[it & 1];
+        a.xi_out = xi[(it + 1) & 1];
+        a.sigma = (float)sigma;
+        a.tau = (float)tau;
+        a.theta = (float)theta;
+        tv_step_kernel<<<grid, 32 * kTvWarps, 0, c.st>>>(a);
         tau *= theta;
         sigma /= theta;
     }

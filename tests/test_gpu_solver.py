@@ -41,16 +41,21 @@ def op_for(g, s):
     return PatOperator(g, s)
 
 
-@pytest.mark.parametrize("shape,alpha,iters", [((32, 32, 32), 0.05, 100), ((16, 32, 8), 0.3, 300),
-                                               ((64, 128, 128), 0.02, 50)])
-def test_tv_prox_matches_oracle(dev, sol, shape, alpha, iters):
-    g = presets.Grid(*shape, T=2, pml_size=1)
+@pytest.mark.parametrize("shape,batch,alpha,iters", [
+    ((32, 32, 32), 1, 0.05, 100), ((16, 32, 8), 1, 0.3, 300), ((64, 128, 128), 1, 0.02, 50),
+    # lines shorter than a warp, batches, many runs of z planes, several x tiles of 32
+    ((8, 16, 16), 2, 0.1, 60), ((256, 8, 8), 1, 0.1, 40), ((8, 8, 256), 1, 0.1, 40)])
+def test_tv_prox_matches_oracle(dev, sol, shape, batch, alpha, iters):
+    """The fused primal-dual kernel (one launch per iteration: z-marching CTAs of 32 x 8 columns,
+    warp-shuffle x neighbours, a halo row and column, runs of z planes) against the oracle's prox."""
+    g = presets.Grid(*shape, T=2, pml_size=1, batch=batch)
     op = op_for(g, presets.Sampling(presets.KIND_FULL, g.m_plane))
-    p = np.random.default_rng(1).standard_normal(shape) * 0.5 + 0.2
+    p = np.random.default_rng(1).standard_normal((batch,) + shape) * 0.5 + 0.2
     x = torch.tensor(p, dtype=torch.float32, device=dev).reshape(op.image_shape)
-    got = op.tv_prox(x, alpha, iters).double().cpu().numpy().reshape(shape)
-    ref = sol.tv_prox(p, alpha, iters)
-    assert rel(got, ref) < 1e-5
+    got = op.tv_prox(x, alpha, iters).double().cpu().numpy().reshape((batch,) + shape)
+    for b in range(batch):
+        ref = sol.tv_prox(p[b], alpha, iters)
+        assert rel(got[b], ref) < 1e-5
     assert got.min() >= 0
 
 

@@ -37,7 +37,7 @@ METRIC = "A+A^T pairs/s (64x128x128, 400 steps)"
 
 # (kernel source hash, workload, batch) -> DRAM bytes (read + write) of one forward time step (x, y and
 # z passes), from ncu with the L2 as the run leaves it (--cache-control none)
-STEP_TRAFFIC = {("3088a9070030", "c2", 1): 4.75e6, ("3088a9070030", "c4", 1): 672.3e6}
+STEP_TRAFFIC = {("00f5b3bcbe10", "c2", 1): 4.84e6, ("00f5b3bcbe10", "c4", 1): 672.3e6}
 UNIT = "pairs/s"
 
 
@@ -60,6 +60,9 @@ def parse():
                          "workload's grid: its tensor-core convolutions against the BF16 roofline")
     ap.add_argument("--unet-only", action="store_true",
                     help="only the U-Net timing (no operator timing, solve or CPU baseline)")
+    ap.add_argument("--prox-only", action="store_true",
+                    help="only the TV prox's timing at the workload's grid (50 primal-dual iterations on the "
+                         "back-projection of the workload's data; the `solve.prox` object alone)")
     ap.add_argument("--warm", action="store_true",
                     help="also train the learned warm start and time warm vs plain solves to 2 %% error")
     ap.add_argument("--warm-train", type=int, default=64)
@@ -233,6 +236,16 @@ def main():
     p0 = torch.tensor(p0_np, device=dev)
     f = torch.empty(op.data_shape, device=dev)
     p = torch.empty(op.image_shape, device=dev)
+    if args.prox_only:
+        op.forward_into(p0, f)
+        op.adjoint_into(f, p)
+        alpha = 1e-3 * float(p.abs().max())
+        res = prox_timing(op, p, alpha, 50)
+        op.device_status(dev)
+        if rank == 0:
+            print(json.dumps({"metric": "TV prox us per iteration", "config": {"workload": w.name},
+                              "alpha": alpha, "prox": res}), flush=True)
+        return 0
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MiB > L2
 
     def step():

@@ -519,12 +519,12 @@ def prox_timing(op, x, alpha, iters, reps=5):
     gbs = 44.0 * voxels / (us * 1e-6) / 1e9
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     peak = float(_json.load(open(peaks_path))["hbm_gbs"]) if os.path.exists(peaks_path) else 6800.0
-    fields = 11 * 4 * voxels  # qbar and the dual twice (read and write buffers), q, the input
+    fields = 10 * 4 * voxels  # qbar and the dual (3) in a read and a write buffer each, q, the input
     where = ("stay in the 129 MB L2 at this size, so the fraction is of the HBM copy bandwidth, not DRAM "
              "traffic") if fields < 100e6 else "exceed the L2 at this size"
     return {"iters": iters, "us_per_iter": us, "voxels": voxels, "algorithmic_bytes_per_voxel": 44,
             "achieved_gbs": gbs, "frac_of_hbm": gbs / peak,
-            "note": f"one launch per iteration; the prox's fields (11 image-sized FP32 arrays, "
+            "note": f"one launch per iteration; the prox's fields (10 image-sized FP32 arrays, "
                     f"{fields / 1e6:.0f} MB) {where}"}
 
 

@@ -65,10 +65,10 @@ def parse():
                          "back-projection of the workload's data; the `solve.prox` object alone)")
     ap.add_argument("--warm", action="store_true",
                     help="also train the learned warm start and time warm vs plain solves to 2 %% error")
-    ap.add_argument("--warm-train", type=int, default=64)
+    ap.add_argument("--warm-train", type=int, default=256)
     ap.add_argument("--warm-test", type=int, default=3)
     ap.add_argument("--warm-epochs", type=int, default=20)
-    ap.add_argument("--warm-target-inner", type=int, default=150,
+    ap.add_argument("--warm-target-inner", type=int, default=100,
                     help="FISTA iterations per Bregman step of the training targets")
     ap.add_argument("--warm-ref-inner", type=int, default=600,
                     help="FISTA iterations per Bregman step of the converged reference")
@@ -494,7 +494,7 @@ def solve_experiment(args, op, f_clean, p0, dev):
             "prox": prox_rate,
             "warm_start": "plain cold-start solve; bench.py --warm trains the learned U-Net warm start and "
                           "times warm against plain against a 5 x 600 reference (the line's warm_start "
-                          "object; about 35 GPU-minutes with 128 training phantoms)"}
+                          "object; about 55 GPU-minutes with the default 256 training phantoms)"}
 
 
 def prox_timing(op, x, alpha, iters, reps=5):

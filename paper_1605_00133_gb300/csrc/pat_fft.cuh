@@ -249,7 +249,8 @@ __device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsign
 }
 // Wait for phase `parity` of an mbarrier to complete: each poll suspends the thread for at most about
 // a microsecond, and after `polls` polls (about a second for 1 << 20) the wait gives up and returns
-// false; the caller records the failure and carries on, so no thread is left waiting.
+// false; the caller records the failure and does not use what the copy should have delivered, so no
+// thread is left waiting.
 __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity, int polls) {
     for (int i = 0; i < polls; i++) {
         unsigned done;

@@ -24,6 +24,11 @@
  *
  * Layout: real fields are [Nz][Ny][Nx] row-major (x fastest); z is the depth axis and the paper's x.
  * Plane series are [T][Ny*Nx].  All arithmetic is double precision.
+ *
+ * Pins (tests/test_oracle_pins.py): every function is pinned against closed forms, brute force or
+ * dense matrices.  Parity unpinned, as readings rather than functions: the absolute reflection
+ * level of the PML profile (a chosen profile with no paper value; only its smallness is checked) and
+ * the particular scrambled-Hadamard variant (a self-consistent reading of the paper's reference).
  */
 #include <complex.h>
 #include <math.h>
